@@ -1,0 +1,465 @@
+#!/usr/bin/env python3
+"""Benchmark: Anderson-acceleration iterations/s on one GB300 (and replicas).
+
+Workload: the 3D anisotropic 7-point weighted-Jacobi fixed point
+(eps_y = 0.1, eps_z = 0.01, omega = 0.8) on a 406^3 grid (n = 66,923,416,
+about 2^26), b ~ U(-1, 1) from seed, x_0 = 0, AA with history depth m = 20,
+FP64.  One "step" is one Anderson iteration at a full history: G(x_i) (the
+stencil map, a library kernel) followed by aa_step (pass A with the QRDelete
+rotation, the projection pass(es), the x update).  The history is filled by
+m untimed iterations before the warm-up, so that every timed step is a
+recycle iteration.
+
+Prints one JSON line (rank 0).  With torchrun (N > 1) each rank runs an
+independent replica of the workload (the solve does not shard); value sums
+the iterations of all ranks over the max-over-ranks time.
+
+--impl reference times the CPU oracle (oracle/, single thread) on a bounded
+slab of the same workload (406 x 406 x 8), scaled to the full n.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NX = NY = NZ = 406
+EY, EZ, OMEGA = 0.1, 0.01, 0.8
+SLAB_NZ = 8  # oracle sample: 406 x 406 x 8 rows of the same stencil problem
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=30)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--orth", default="icwy", choices=["mgs", "icwy", "cgs2", "dcgs2"])
+    p.add_argument("--m", type=int, default=20)
+    p.add_argument("--storage", default="fp64", choices=["fp64", "fp32", "bf16"])
+    p.add_argument("--nz", type=int, default=NZ)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--cpu-iters", type=int, default=12)
+    return p.parse_args()
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# FP64 peak derived from unit counts and clocks: 2 DFMA / clock / SM x
+# 2 flop x 152 SMs x 2.07 GHz.
+FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def pass_bytes(kind: str, n: int, m: int, esz: int, orth: str) -> float:
+    """Algorithmic HBM bytes of one launch at a full history (recycle)."""
+    k = m - 1
+    if kind == "A":  # read x, g, g_prev, f_prev, m slots; write dg, df, f, g, k slots
+        return n * (4 * 8 + m * esz + esz + 3 * 8 + k * esz)
+    if kind == "proj":  # read w, f, k slots (MGS: 1); write new slot (+ DCGS-2 q_{k-1})
+        cols = 1 if orth == "mgs" else k
+        extra = esz if orth == "dcgs2" else 0
+        return n * (2 * 8 + cols * esz + esz + extra)
+    if kind == "cgs2b":  # read w, k slots; write y
+        return n * (8 + k * esz + 8)
+    if kind == "mgs":  # read v, 2 slots; write v
+        return n * (8 + 2 * esz + 8)
+    if kind == "update":  # read g, m dG slots; write x
+        return n * (8 + m * esz + 8)
+    return 0.0
+
+
+def pass_flops(kind: str, n: int, m: int, orth: str) -> float:
+    """Algorithmic FP64 flops of one launch at a full history."""
+    k = m - 1
+    if kind == "A":
+        rot = 6 * (m - 1) + 1
+        diffs = 3
+        dots = 3 + 2 * k + (k - 1 if orth in ("icwy", "dcgs2") else 0)
+        if orth == "mgs":
+            dots = 3 + k + 1
+        return n * (rot + diffs + 2 * dots)
+    if kind == "proj":
+        cols = 1 if orth == "mgs" else k
+        re = 2 * (k - 1) + 1 if orth == "dcgs2" else 0
+        return n * (2 * cols + re + 2 * (2 + (orth == "dcgs2")))
+    if kind == "cgs2b":
+        return n * 4 * k
+    if kind == "mgs":
+        return n * 4
+    if kind == "update":
+        return n * 2 * m
+    return 0.0
+
+
+def run_ours(args, ws, rank, local):
+    import numpy as np
+    import torch
+
+    import aa_synth
+    import paper_2110_09667_gb300 as aa
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    nx, ny, nz = NX, NY, args.nz
+    n = nx * ny * nz
+    esz = {"fp64": 8, "fp32": 4, "bf16": 2}[args.storage]
+    b_h = aa_synth.jacobi3d_rhs(0, nx, ny, nz)
+    b = torch.from_numpy(b_h).to(dev)
+    del b_h
+    P = aa.Jacobi3D(nx, ny, nz, EY, EZ, OMEGA, b.data_ptr())
+    gfn = aa.builtin_g("aa_g_jacobi3d")
+    Pp = aa.C.cast(aa.C.pointer(P), aa.C.c_void_p)
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+    A = aa.Anderson(n, args.m, args.orth, args.storage, flags=aa.FLAG_TIMING, max_iters=10**6)
+    x = torch.zeros(n, dtype=torch.float64, device=dev)
+    xn = torch.empty_like(x)
+    g = torch.empty_like(x)
+
+    def one_step():
+        nonlocal x, xn
+        rc = gfn(x.data_ptr(), g.data_ptr(), n, sp, Pp)
+        if rc != 0:
+            raise RuntimeError(f"G failed: {rc}")
+        fn = A.step(x, g, xn)
+        x, xn = xn, x
+        return fn
+
+    # fill the history (m + 1 steps), then warm up
+    for _ in range(args.m + 1):
+        one_step()
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    pt0 = A.pass_times()
+    st0 = A.stats()
+    clocks = Clocks(local)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    fn = 0.0
+    for _ in range(args.steps):
+        fn = one_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    st1 = A.stats()
+    pt1 = A.pass_times()
+    launches = (st1["launches"] - st0["launches"]) + args.steps  # + one G kernel per step
+    per_kind = {}
+    for kd, (tms, cnt) in pt1.items():
+        t0, c0 = pt0.get(kd, (0.0, 0))
+        if cnt - c0 > 0:
+            per_kind[kd] = {"ms_total": tms - t0, "launches": cnt - c0,
+                            "ms_avg": (tms - t0) / (cnt - c0)}
+    total_pass_ms = sum(v["ms_total"] for v in per_kind.values())
+    # dominant kernel
+    dom = max(per_kind, key=lambda kd: per_kind[kd]["ms_total"])
+    d = per_kind[dom]
+    hbm_peak, peak_src = measured_peaks()
+    bytes_l = pass_bytes(dom, n, args.m, esz, args.orth)
+    flops_l = pass_flops(dom, n, args.m, args.orth)
+    gbs = bytes_l / (d["ms_avg"] * 1e-3) / 1e9
+    tflops = flops_l / (d["ms_avg"] * 1e-3) / 1e12
+    hbm_frac = gbs / hbm_peak
+    fp64_frac = tflops / FP64_PEAK_TFLOPS
+    traffic = None
+    tr_path = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tr_path):
+        try:
+            with open(tr_path) as f:
+                tr = json.load(f)
+            key = f"{args.orth}_{args.storage}_m{args.m}_{dom}"
+            if key in tr:
+                traffic = tr[key]["bytes_per_launch_full_n"]
+        except Exception:
+            traffic = None
+    if fp64_frac > hbm_frac:
+        roof = {"bound": "alu", "achieved": round(tflops, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
+                "unit": "TFLOP/s", "frac": round(fp64_frac, 4), "traffic": traffic,
+                "peak_source": "FP64 pipe: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (derived)",
+                "kernel": f"pass_{dom}",
+                "hbm": {"achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+                        "frac": round(hbm_frac, 4), "peak_source": peak_src}}
+    else:
+        roof = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(hbm_frac, 4), "traffic": traffic, "peak_source": peak_src,
+                "kernel": f"pass_{dom}",
+                "fp64": {"achieved": round(tflops, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
+                         "unit": "TFLOP/s", "frac": round(fp64_frac, 4)}}
+    # whole-step HBM rate over the AA passes
+    step_bytes = sum(pass_bytes(kd, n, args.m, esz, args.orth) * v["launches"]
+                     for kd, v in per_kind.items())
+    aa_gbs = step_bytes / (total_pass_ms * 1e-3) / 1e9 if total_pass_ms > 0 else None
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, A, gfn, Pp, n, dev, stream, one_step_state=(x, xn, g))
+    wall = run_wall_to_tol(aa, args, dev) if rank == 0 else None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank != 0:
+        return None
+    value = args.steps * ws / (ms * 1e-3)
+    line = {
+        "metric": f"AA iterations/s (3D 7-pt weighted Jacobi, n=406^3~2^26, m={args.m}, "
+                  f"{args.orth.upper()})",
+        "value": round(value, 3),
+        "unit": "iter/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms / args.steps, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64" if args.storage == "fp64" else f"f64 ({args.storage} history storage)",
+        "data": "synthetic (seeded SplitMix64 b ~ U(-1,1), x0 = 0)",
+        "config": {"workload": f"AA({args.m}) {args.orth} on 3D 7-pt weighted Jacobi "
+                               f"{nx}x{ny}x{nz}, recycle iterations",
+                   "n": n, "m": args.m, "orth": args.orth, "storage": args.storage,
+                   "parallelism": f"replicas x{ws}",
+                   "l2": "inputs larger than L2 (history %.1f GB per replica)"
+                         % (2 * n * args.m * esz / 1e9),
+                   "step": "G(x) + aa_step (pass A, projection, update)"},
+        "roofline": roof,
+        "passes": {kd: {"ms_avg": round(v["ms_avg"], 4), "launches": v["launches"],
+                        "share": round(v["ms_total"] / total_pass_ms, 4)}
+                   for kd, v in per_kind.items()},
+        "aa_passes_gbs": round(aa_gbs, 1) if aa_gbs else None,
+        "aa_passes_ms_per_step": round(total_pass_ms / args.steps, 4),
+        "fnorm_last": fn,
+        "gpu_launches": int(launches),
+        "clocks": ck,
+        "e2e": e2e,
+        "wall_to_1e-8": wall,
+    }
+    if not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(args)
+    return line
+
+
+def run_e2e(args, A, gfn, Pp, n, dev, stream, one_step_state):
+    """Same metric through the public API with host buffers: every step
+    copies x_i from pinned host memory, evaluates G, runs aa_step and reads
+    x_{i+1} back into pinned host memory."""
+    import torch
+    x, xn, g = one_step_state
+    xh = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    xh.copy_(x)
+    sp = stream.cuda_stream
+    steps = max(3, min(args.steps, 20))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        x.copy_(xh, non_blocking=True)
+        gfn(x.data_ptr(), g.data_ptr(), n, sp, Pp)
+        A.step(x, g, xn)
+        xh.copy_(xn, non_blocking=True)
+        torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    return {"value": round(steps / dt, 3), "unit": "iter/s", "steps": steps,
+            "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n + 8,
+            "api": "aa_step with host-resident x (pinned), G on device"}
+
+
+def run_wall_to_tol(aa, args, dev):
+    """Wall time to ||f||/||b|| < 1e-8 on the 64 x 64 anisotropic Jacobi
+    problem, AA(5), through aa_solve."""
+    import numpy as np
+    import torch
+
+    import aa_synth
+    nx = ny = 64
+    n = nx * ny
+    b = aa_synth.jacobi2d_rhs(0, nx, ny)
+    scale = float(np.linalg.norm(b))
+    bd = torch.from_numpy(b).to(dev)
+    P = aa.Jacobi2D(nx, ny, 0.01, bd.data_ptr())
+    out = {}
+    for orth in ("mgs", args.orth):
+        A = aa.Anderson(n, 5, orth, tol=1e-8, scale=scale, max_iters=500)
+        x = torch.zeros(n, dtype=torch.float64, device=dev)
+        A.solve(aa.builtin_g("aa_g_jacobi2d"), P, x)  # warm
+        x.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc, st = A.solve(aa.builtin_g("aa_g_jacobi2d"), P, x)
+        torch.cuda.synchronize()
+        out[orth] = {"ms": round((time.perf_counter() - t0) * 1e3, 3), "iters": st["iters"],
+                     "converged": rc == 0}
+        A.close()
+    return {"workload": "64x64 2D anisotropic Jacobi, AA(5), tol 1e-8", **out}
+
+
+def oracle_sample(args, iters: int, warm: int):
+    """Time the CPU oracle on a 406 x 406 x SLAB_NZ slab of the workload.
+    Returns (seconds per recycle iteration on the slab, slab n)."""
+    import numpy as np
+
+    import aa_synth
+    import oracle
+    nx, ny, nz = NX, NY, SLAB_NZ
+    n = nx * ny * nz
+    b = aa_synth.jacobi3d_rhs(0, nx, ny, nz)
+    O = oracle.Oracle(n, args.m, args.orth, store_round={"fp64": 0, "fp32": 1, "bf16": 2}[args.storage])
+    x = np.zeros(n)
+    for _ in range(args.m + 1 + warm):
+        g = oracle.g_jacobi3d(nx, ny, nz, EY, EZ, OMEGA, b, x)
+        x, _, _ = O.step(x, g)
+    t = []
+    for _ in range(iters):
+        t0 = time.perf_counter()
+        g = oracle.g_jacobi3d(nx, ny, nz, EY, EZ, OMEGA, b, x)
+        x, _, _ = O.step(x, g)
+        t.append(time.perf_counter() - t0)
+    O.close()
+    return t, n
+
+
+def cpu_baseline(args):
+    t, ns = oracle_sample(args, args.cpu_iters, 0)
+    n = NX * NY * args.nz
+    per_iter_full = statistics.median(t) * n / ns
+    return {"value": round(1.0 / per_iter_full, 5), "unit": "iter/s", "cores": 1,
+            "kind": "oracle",
+            "sample": f"{len(t)} recycle AA({args.m}) {args.orth} iterations (G + step) of the "
+                      f"oracle on a {NX}x{NY}x{SLAB_NZ} slab of the same stencil problem "
+                      f"(n={ns}), median time scaled by n to the full {n}-row workload",
+            "slab_s_per_iter_median": round(statistics.median(t), 4)}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return None
+    t, ns = oracle_sample(args, args.steps, args.warmup)
+    n = NX * NY * args.nz
+    total_full = sum(t) * n / ns
+    value = args.steps / total_full
+    return {
+        "impl": "reference",
+        "metric": f"AA iterations/s (3D 7-pt weighted Jacobi, n=406^3~2^26, m={args.m}, "
+                  f"{args.orth.upper()})",
+        "value": round(value, 5), "unit": "iter/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(total_full / args.steps * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded SplitMix64 b ~ U(-1,1), x0 = 0)",
+        "config": {"workload": f"AA({args.m}) {args.orth} on 3D 7-pt weighted Jacobi "
+                               f"{NX}x{NY}x{args.nz}, recycle iterations",
+                   "n": n, "m": args.m, "orth": args.orth, "storage": args.storage},
+        "cpu_baseline": {"value": round(value, 5), "unit": "iter/s", "cores": 1,
+                         "kind": "oracle",
+                         "sample": f"each step: one recycle iteration (G + step) of the CPU "
+                                   f"oracle on a {NX}x{NY}x{SLAB_NZ} slab (n={ns}), time scaled "
+                                   f"by n to the full workload"},
+        "e2e": {"value": round(value, 5), "unit": "iter/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        line = run_reference(args, ws, rank)
+    else:
+        line = run_ours(args, ws, rank, local)
+    if line is not None and rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

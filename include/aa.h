@@ -1,0 +1,192 @@
+/*
+ * aa.h -- C ABI of the GB300 (sm_103a) low-synchronization Anderson
+ * acceleration library (libaa).
+ *
+ * Method: Anderson acceleration (Algorithm 1 of Lockhart et al., arXiv
+ * 2110.09667) whose least-squares problem (Algorithm 2) is solved through a
+ * QR factorization of the residual-difference history F_i that is updated
+ * in place each iteration: QRDelete drops the oldest column by Givens
+ * rotations, QRAdd appends Delta f_{i-1} with one of four orthogonalization
+ * schemes -- MGS (Algorithm 3), ICWY (Algorithm 4), CGS-2 (Algorithm 5),
+ * DCGS-2 (Algorithm 6).
+ *
+ * Conventions for every entry point:
+ *  - Pointers named *_dev are device pointers (cudaMalloc / torch CUDA
+ *    tensors) on the current device, 16-byte aligned, holding n contiguous
+ *    FP64 values unless stated otherwise.  *_host pointers are host memory.
+ *  - All device work is enqueued on the context's stream (aa_config.stream,
+ *    a cudaStream_t; NULL means the legacy default stream).  Calls return
+ *    after enqueueing, except where a host output is requested: those
+ *    synchronize the stream before returning.
+ *  - Return value: 0 (AA_OK) on success, 1 (AA_NOTCONVERGED) from aa_solve
+ *    when max_iters is reached, a negative AA_E* code on error.  No C++
+ *    exception crosses the ABI.  aa_last_error() gives a message.
+ *  - A context is not thread-safe; distinct contexts are independent.
+ *  - The caller owns x, G(x), f and user data; the context owns the history
+ *    (Q, R, T, dG, f_{i-1}, G(x_{i-1})) and its reduction scratch.
+ */
+#ifndef AA_H_
+#define AA_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define AA_OK 0
+#define AA_NOTCONVERGED 1
+#define AA_EINVAL (-1)     /* bad argument (size, alignment, enum, NULL) */
+#define AA_ENOMEM (-2)     /* device or host allocation failed */
+#define AA_ECUDA (-3)      /* a CUDA runtime call failed */
+#define AA_EBREAKDOWN (-4) /* QRAdd: new column numerically in span(Q); history cleared */
+#define AA_ENONFINITE (-5) /* NaN/Inf in a residual or norm */
+#define AA_ETIMEOUT (-6)   /* a bounded device-side wait ran out */
+#define AA_ECALLBACK (-7)  /* the user's G callback returned non-zero */
+#define AA_ESTATE (-8)     /* call not valid in the context's current state */
+
+/* Orthogonalization scheme used by QRAdd (Sec. 3 of the paper). */
+typedef enum { AA_MGS = 0, AA_ICWY = 1, AA_CGS2 = 2, AA_DCGS2 = 3 } aa_orth;
+
+/* Storage type of the history Q and dG.  Dot products, norms, R, T and
+ * gamma stay FP64 in every case; x, G(x), f and Delta f stay FP64. */
+typedef enum { AA_STORE_FP64 = 0, AA_STORE_FP32 = 1, AA_STORE_BF16 = 2 } aa_storage;
+
+/* Flags (aa_config.flags). */
+#define AA_FLAG_DCGS2_SCALED 0x1u  /* DCGS-2: R_{0:k-2,k-1} += R_{k-1,k-1} s instead of += s */
+#define AA_FLAG_ICWY_GRAM 0x2u     /* ICWY: after a delete, refresh T from a Gram reduction of
+                                      the rotated Q (fused into the first pass, k <= 24) instead
+                                      of rotating T at the m x m level */
+#define AA_FLAG_TIMING 0x4u        /* record CUDA events around every pass (aa_pass_times) */
+
+typedef struct aa_config {
+  int64_t n;          /* vector length, >= 1 */
+  int32_t m;          /* history depth, 1..64 */
+  int32_t orth;       /* aa_orth */
+  int32_t storage;    /* aa_storage */
+  int32_t max_iters;  /* aa_solve: iteration cap (>= 0) */
+  double tol;         /* aa_solve: stop when ||G(x_i) - x_i||_2 / scale < tol (stop_kind 0)
+                         or ||x_{i+1} - x_i||_2 < tol (stop_kind 1, Algorithm 1 as printed) */
+  double scale;       /* > 0; typically ||b||_2 */
+  int32_t stop_kind;  /* 0 or 1 */
+  int32_t dcgs2_min_mi; /* DCGS-2 reorthogonalises when m_i > this; the paper uses 3 */
+  double breakdown_tol; /* breakdown when rho <= breakdown_tol * ||Delta f||; default 1e-14 when 0 */
+  uint64_t flags;     /* AA_FLAG_* */
+  void *stream;       /* cudaStream_t */
+} aa_config;
+
+/* Fills cfg with defaults: m=5, MGS, FP64, max_iters=100, tol=1e-8, scale=1,
+ * stop_kind=0, dcgs2_min_mi=3, breakdown_tol=1e-14, flags=0, stream=NULL. */
+void aa_config_default(aa_config *cfg, int64_t n);
+
+typedef struct aa_ctx aa_ctx;
+
+/* Per-context counters, cumulative since aa_create / aa_reset. */
+typedef struct aa_stats {
+  int64_t iters;          /* aa_solve: iterations taken (x_0 is iterate 0) */
+  int64_t steps;          /* aa_step calls */
+  int64_t reductions;     /* grid-wide reduction passes (the paper's "syncs") */
+  int64_t launches;       /* kernels launched by the library */
+  int64_t breakdowns;     /* history restarts */
+  double fnorm;           /* ||f_i||_2 of the last step */
+  double g_ms, aa_ms;     /* aa_solve: time in G and in the AA passes (CUDA events) */
+} aa_stats;
+
+/* Create a context: allocates and zeroes the history on the current device.
+ * Errors: AA_EINVAL (n < 1, m outside 1..64, bad enum), AA_ENOMEM, AA_ECUDA. */
+int aa_create(const aa_config *cfg, aa_ctx **out);
+
+/* Destroy a context (synchronizes its stream, frees all device memory).  NULL is ignored. */
+void aa_destroy(aa_ctx *ctx);
+
+/* Forget the history (Algorithm 1 restarts at iteration 0). */
+int aa_reset(aa_ctx *ctx);
+
+/* Replace the stream used by later calls. */
+int aa_set_stream(aa_ctx *ctx, void *stream);
+
+/* Algorithm 2, QR part, as a unit: if the factorization already holds m
+ * columns, QRDelete removes the oldest (Givens rotations); then QRAdd
+ * appends v_dev with the configured scheme.  v_dev (n FP64) is only read.
+ * Returns AA_EBREAKDOWN (history cleared) when the new column's norm is
+ * <= breakdown_tol * ||v||.  Synchronizes the stream. */
+int aa_qradd(aa_ctx *ctx, const double *v_dev);
+
+/* Algorithm 2, last step: gamma_host[0..k-1] solves R gamma = Q^T f_dev for
+ * the k columns held.  Returns k (>= 0) or a negative error.  Synchronizes. */
+int aa_lsq(aa_ctx *ctx, const double *f_dev, double *gamma_host);
+
+/* One iteration of Algorithm 1 given x_i (x_dev) and G(x_i) (gx_dev): forms
+ * f_i, Delta f_{i-1}, Delta g_{i-1}, updates the QR factorization and the dG
+ * history, solves the least-squares problem and writes
+ * x_{i+1} = G(x_i) - dG_i gamma into xnext_dev (which must not alias x_dev
+ * or gx_dev).  The first call after create/reset writes x_1 = G(x_0).
+ * *fnorm_host (if not NULL) receives ||f_i||_2; then the stream is
+ * synchronized.  AA_EBREAKDOWN is not returned: a breakdown clears the
+ * history and the step falls back to x_{i+1} = G(x_i) (counted in stats). */
+int aa_step(aa_ctx *ctx, const double *x_dev, const double *gx_dev, double *xnext_dev,
+            double *fnorm_host);
+
+/* User fixed-point map: enqueue gx_dev = G(x_dev) on `stream` and return 0;
+ * any non-zero return aborts aa_solve with AA_ECALLBACK. */
+typedef int (*aa_g_fn)(const double *x_dev, double *gx_dev, int64_t n, void *stream, void *user);
+
+/* Algorithm 1 to convergence: x_dev holds x_0 on entry and the returned
+ * iterate on exit.  Returns AA_OK, AA_NOTCONVERGED, or an error. */
+int aa_solve(aa_ctx *ctx, aa_g_fn G, void *user, double *x_dev, aa_stats *stats);
+
+/* Current factorization for inspection: Q_host (n x k, column-major, may be
+ * NULL), R_host (k x k row-major, may be NULL), T_host (ICWY's unit-lower
+ * T, k x k row-major, may be NULL); *k receives the column count. Synchronizes. */
+int aa_get_qr(aa_ctx *ctx, double *Q_host, double *R_host, double *T_host, int *k);
+
+/* Counters since create/reset. */
+int aa_get_stats(const aa_ctx *ctx, aa_stats *out);
+
+/* Per-pass device time (AA_FLAG_TIMING): ms_out[kind] and count_out[kind]
+ * accumulate, for each pass kind (0 init, 1 first pass, 2 projection,
+ * 3 CGS-2 middle pass, 4 MGS link, 5 update, 6 lsq, 7 mdot), the CUDA-event
+ * time measured on the context's stream and the number of launches since
+ * create/reset.  Both arrays hold 8 entries. */
+int aa_pass_times(const aa_ctx *ctx, double *ms_out, int64_t *count_out);
+
+/* Multi-column dot product with a deterministic two-stage grid reduction
+ * (the fused multi-dot of Sec. 4): out_host[j*nv + v] = sum_i A_j[i] * V_v[i]
+ * for the k columns A_j = A_dev + j*lda and nv vectors V_v = V_dev + v*ldv
+ * (all FP64, columns 16-byte aligned, k*nv <= 256, lda, ldv >= n).  The
+ * result is bit-identical from run to run.  Allocates its reduction scratch
+ * (grid x k*nv doubles) with cudaMalloc on every call.  Synchronizes. */
+int aa_mdot(const double *A_dev, int64_t lda, int k, const double *V_dev, int64_t ldv, int nv,
+            int64_t n, double *out_host, void *stream);
+
+/* ---------------------------------------------------------- test problems
+ * Built-in fixed-point maps (aa_g_fn-compatible) for the seeded stencil
+ * workloads.  `user` points to the matching parameter struct; b/src are
+ * device pointers. */
+typedef struct aa_jacobi2d {  /* 2D 5-point anisotropic Jacobi: G = x + D^{-1}(b - A x) */
+  int64_t nx, ny; double eps; const double *b_dev;
+} aa_jacobi2d;
+typedef struct aa_jacobi3d {  /* 3D 7-point weighted Jacobi: G = x + omega D^{-1}(b - A x) */
+  int64_t nx, ny, nz; double ey, ez, omega; const double *b_dev;
+} aa_jacobi3d;
+typedef struct aa_bratu2d {   /* nonlinear Jacobi for -Lap u = lambda e^u + src, h = 1/(s+1) */
+  int64_t s; double lambda; const double *src_dev; /* src may be NULL */
+} aa_bratu2d;
+
+int aa_g_jacobi2d(const double *x_dev, double *gx_dev, int64_t n, void *stream, void *user);
+int aa_g_jacobi3d(const double *x_dev, double *gx_dev, int64_t n, void *stream, void *user);
+int aa_g_bratu2d(const double *x_dev, double *gx_dev, int64_t n, void *stream, void *user);
+
+/* Message for the last error on this thread. */
+const char *aa_last_error(void);
+const char *aa_strerror(int code);
+
+/* Library version string. */
+const char *aa_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AA_H_ */

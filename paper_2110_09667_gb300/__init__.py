@@ -1,0 +1,217 @@
+"""GB300-native low-synchronization Anderson acceleration (arXiv 2110.09667).
+
+Python binding of libaa (include/aa.h): argument marshalling only.  Every
+step of the Anderson iteration runs in the library's sm_103a kernels; this
+module passes device pointers (``tensor.data_ptr()``) and the current CUDA
+stream.  There is no CPU fallback: importing the binding fails loudly if the
+shared library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes as C  # noqa: N812
+import os
+
+from .build import LIB
+
+__all__ = ["Anderson", "lib", "mdot", "AAError", "ORTH", "STORAGE",
+           "Jacobi2D", "Jacobi3D", "Bratu2D"]
+
+ORTH = {"mgs": 0, "icwy": 1, "cgs2": 2, "dcgs2": 3}
+STORAGE = {"fp64": 0, "fp32": 1, "bf16": 2}
+FLAG_DCGS2_SCALED = 0x1
+FLAG_ICWY_GRAM = 0x2
+FLAG_TIMING = 0x4
+PASS_KINDS = ["init", "A", "proj", "cgs2b", "mgs", "update", "lsq", "mdot"]
+
+AA_OK, AA_NOTCONVERGED = 0, 1
+AA_EBREAKDOWN = -4
+
+
+class AAError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libaa error {code}: {msg}")
+        self.code = code
+
+
+class Config(C.Structure):
+    _fields_ = [("n", C.c_int64), ("m", C.c_int32), ("orth", C.c_int32), ("storage", C.c_int32),
+                ("max_iters", C.c_int32), ("tol", C.c_double), ("scale", C.c_double),
+                ("stop_kind", C.c_int32), ("dcgs2_min_mi", C.c_int32),
+                ("breakdown_tol", C.c_double), ("flags", C.c_uint64), ("stream", C.c_void_p)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("iters", C.c_int64), ("steps", C.c_int64), ("reductions", C.c_int64),
+                ("launches", C.c_int64), ("breakdowns", C.c_int64), ("fnorm", C.c_double),
+                ("g_ms", C.c_double), ("aa_ms", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Jacobi2D(C.Structure):
+    _fields_ = [("nx", C.c_int64), ("ny", C.c_int64), ("eps", C.c_double), ("b_dev", C.c_void_p)]
+
+
+class Jacobi3D(C.Structure):
+    _fields_ = [("nx", C.c_int64), ("ny", C.c_int64), ("nz", C.c_int64), ("ey", C.c_double),
+                ("ez", C.c_double), ("omega", C.c_double), ("b_dev", C.c_void_p)]
+
+
+class Bratu2D(C.Structure):
+    _fields_ = [("s", C.c_int64), ("lam", C.c_double), ("src_dev", C.c_void_p)]
+
+
+GFN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p)
+_dp = C.POINTER(C.c_double)
+_lib = None
+
+
+def lib():
+    """Load libaa.so; raises ImportError if it was not built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            raise ImportError(f"libaa.so not found at {LIB}: run __graft_entry__.build() "
+                              "(or python -m paper_2110_09667_gb300.build)")
+        L = C.CDLL(LIB)
+        L.aa_config_default.argtypes = [C.POINTER(Config), C.c_int64]
+        L.aa_create.argtypes = [C.POINTER(Config), C.POINTER(C.c_void_p)]
+        L.aa_destroy.argtypes = [C.c_void_p]
+        L.aa_reset.argtypes = [C.c_void_p]
+        L.aa_set_stream.argtypes = [C.c_void_p, C.c_void_p]
+        L.aa_qradd.argtypes = [C.c_void_p, C.c_void_p]
+        L.aa_lsq.argtypes = [C.c_void_p, C.c_void_p, _dp]
+        L.aa_step.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, _dp]
+        L.aa_solve.argtypes = [C.c_void_p, GFN, C.c_void_p, C.c_void_p, C.POINTER(Stats)]
+        L.aa_get_qr.argtypes = [C.c_void_p, _dp, _dp, _dp, C.POINTER(C.c_int)]
+        L.aa_get_stats.argtypes = [C.c_void_p, C.POINTER(Stats)]
+        L.aa_pass_times.argtypes = [C.c_void_p, _dp, C.POINTER(C.c_int64)]
+        L.aa_mdot.argtypes = [C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_int64, C.c_int,
+                              C.c_int64, _dp, C.c_void_p]
+        for nm in ("aa_g_jacobi2d", "aa_g_jacobi3d", "aa_g_bratu2d"):
+            getattr(L, nm).argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]
+        L.aa_last_error.restype = C.c_char_p
+        L.aa_strerror.restype = C.c_char_p
+        L.aa_version.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(rc: int, allow=(AA_OK,)) -> int:
+    if rc in allow:
+        return rc
+    if rc != AA_OK:
+        raise AAError(rc, lib().aa_last_error().decode())
+    return rc
+
+
+def _stream():
+    import torch
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t) -> C.c_void_p:
+    return C.c_void_p(t.data_ptr())
+
+
+def builtin_g(name: str):
+    """C function pointer of a built-in map (aa_g_jacobi2d/3d, aa_g_bratu2d)."""
+    return GFN(C.cast(getattr(lib(), name), C.c_void_p).value)
+
+
+class Anderson:
+    """One Anderson-acceleration context (aa_create ... aa_destroy)."""
+
+    def __init__(self, n: int, m: int, orth: str = "mgs", storage: str = "fp64", *,
+                 tol: float = 1e-8, scale: float = 1.0, max_iters: int = 100,
+                 stop_kind: int = 0, dcgs2_min_mi: int = 3, breakdown_tol: float = 1e-14,
+                 flags: int = 0, stream=None):
+        L = lib()
+        cfg = Config()
+        L.aa_config_default(C.byref(cfg), int(n))
+        cfg.m, cfg.orth, cfg.storage = int(m), ORTH[orth], STORAGE[storage]
+        cfg.tol, cfg.scale, cfg.max_iters = float(tol), float(scale), int(max_iters)
+        cfg.stop_kind, cfg.dcgs2_min_mi = int(stop_kind), int(dcgs2_min_mi)
+        cfg.breakdown_tol, cfg.flags = float(breakdown_tol), int(flags)
+        cfg.stream = stream if stream is not None else _stream()
+        h = C.c_void_p()
+        _check(L.aa_create(C.byref(cfg), C.byref(h)))
+        self._h = h
+        self.n, self.m = int(n), int(m)
+        self.cfg = cfg
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().aa_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream=None):
+        _check(lib().aa_set_stream(self._h, stream if stream is not None else _stream()))
+
+    def reset(self):
+        _check(lib().aa_reset(self._h))
+
+    def qradd(self, v) -> int:
+        return _check(lib().aa_qradd(self._h, _ptr(v)), allow=(AA_OK, AA_EBREAKDOWN))
+
+    def lsq(self, f):
+        import numpy as np
+        g = (C.c_double * max(self.m, 1))()
+        k = _check(lib().aa_lsq(self._h, _ptr(f), g), allow=tuple(range(0, self.m + 1)))
+        return np.array(g[:k])
+
+    def step(self, x, gx, xnext) -> float:
+        fn = C.c_double(0.0)
+        _check(lib().aa_step(self._h, _ptr(x), _ptr(gx), _ptr(xnext), C.byref(fn)))
+        return fn.value
+
+    def solve(self, gfn, user, x):
+        """aa_solve with a C function pointer (builtin_g) and its parameter struct."""
+        st = Stats()
+        rc = lib().aa_solve(self._h, gfn, C.cast(C.pointer(user), C.c_void_p) if user is not None
+                            else None, _ptr(x), C.byref(st))
+        _check(rc, allow=(AA_OK, AA_NOTCONVERGED))
+        return rc, st.as_dict()
+
+    def get_qr(self):
+        import numpy as np
+        k = C.c_int(0)
+        _check(lib().aa_get_qr(self._h, None, None, None, C.byref(k)))
+        k = k.value
+        Q = np.zeros((max(k, 1), self.n))
+        R = np.zeros((max(k, 1), max(k, 1)))
+        T = np.zeros((max(k, 1), max(k, 1)))
+        kk = C.c_int(0)
+        _check(lib().aa_get_qr(self._h, Q.ctypes.data_as(_dp), R.ctypes.data_as(_dp),
+                               T.ctypes.data_as(_dp), C.byref(kk)))
+        return Q[:k].T.copy(), R[:k, :k].copy(), T[:k, :k].copy()
+
+    def pass_times(self) -> dict:
+        """{kind: (total ms, launches)} from AA_FLAG_TIMING events."""
+        ms = (C.c_double * 8)()
+        cnt = (C.c_int64 * 8)()
+        _check(lib().aa_pass_times(self._h, ms, cnt))
+        return {PASS_KINDS[i]: (ms[i], cnt[i]) for i in range(8) if cnt[i]}
+
+    def stats(self) -> dict:
+        st = Stats()
+        _check(lib().aa_get_stats(self._h, C.byref(st)))
+        return st.as_dict()
+
+
+def mdot(A, V):
+    """A^T V for FP64 CUDA tensors A (k x n, rows are columns) and V (nv x n)."""
+    import numpy as np
+    k, n = A.shape
+    nv = V.shape[0]
+    out = np.zeros(k * nv)
+    _check(lib().aa_mdot(_ptr(A), A.stride(0), k, _ptr(V), V.stride(0), nv, n,
+                         out.ctypes.data_as(_dp), _stream()))
+    return out.reshape(k, nv)

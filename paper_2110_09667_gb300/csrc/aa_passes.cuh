@@ -1,0 +1,846 @@
+#pragma once
+// aa_passes.cuh -- streaming-pass kernels of the low-synchronization
+// Anderson-acceleration hot path for sm_103a.
+//
+// One kernel template serves every pass.  A persistent grid walks row tiles
+// of TR rows.  For each tile one thread issues bulk asynchronous copies
+// (cp.async.bulk, completion on an mbarrier) of the pass's columns into a
+// shared-memory stage; STAGES stages keep the next tile's copies in flight
+// while the current tile is processed.  The per-row program runs one thread
+// per row and writes its outputs straight to global memory with coalesced
+// stores; the dot phase then has each warp accumulate a subset of the
+// pass's dot products over the tile.  At the end every CTA writes its
+// per-dot partial sums to a slot array; the last CTA to take a ticket sums
+// the slots in CTA order -- a deterministic grid-wide reduction, the
+// single-GPU form of the paper's global reduction -- and runs the small
+// m x m part of the algorithm (R, T, gamma) in the same launch.
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "aa_common.h"
+
+
+
+namespace aa {
+
+// Error codes raised on the device (mirror of aa.h).
+constexpr int DEV_ENONFINITE = -5;
+constexpr int DEV_ETIMEOUT = -6;
+
+// ------------------------------------------------------------ conversions
+
+template <class QT> __device__ __forceinline__ double to_d(QT v);
+template <> __device__ __forceinline__ double to_d<double>(double v) { return v; }
+template <> __device__ __forceinline__ double to_d<float>(float v) { return (double)v; }
+template <> __device__ __forceinline__ double to_d<__nv_bfloat16>(__nv_bfloat16 v) {
+  return (double)__bfloat162float(v);
+}
+template <class QT> __device__ __forceinline__ QT from_d(double v);
+template <> __device__ __forceinline__ double from_d<double>(double v) { return v; }
+template <> __device__ __forceinline__ float from_d<float>(double v) { return __double2float_rn(v); }
+template <> __device__ __forceinline__ __nv_bfloat16 from_d<__nv_bfloat16>(double v) {
+  return __float2bfloat16_rn(__double2float_rn(v));
+}
+
+// ------------------------------------------------- mbarrier / bulk copies
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+  uint64_t state;
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;"
+               : "=l"(state)
+               : "r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+  (void)state;
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes,
+                                         uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, "
+      "0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait (about a second at most): on expiry the pass records
+// DEV_ETIMEOUT and the caller stops issuing work.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+  for (uint32_t i = 0; i < (1u << 22); ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (i > 32) __nanosleep(256);
+  }
+  return false;
+}
+
+// ------------------------------------------------------------- tile access
+
+struct Stage {
+  unsigned char *base;
+  __device__ __forceinline__ double *d(int c) const { return (double *)(base + (size_t)c * TR * 8); }
+  template <class QT>
+  __device__ __forceinline__ QT *q(int c) const {
+    return (QT *)(base + (size_t)c * TR * 8);
+  }
+};
+
+template <class QT>
+__device__ __forceinline__ int col_esz(const PassArgs &a, int c) {
+  return c >= a.qbase ? (int)sizeof(QT) : 8;
+}
+
+// Issue the bulk copies of tile t into stage st (one thread).  Rows are
+// copied in multiples of 8 (16 bytes for the narrowest storage type); the
+// remaining < 8 rows of a ragged last tile are loaded by their threads.
+template <class QT>
+static __device__ void issue_tile(const PassArgs &a, Stage st, int t, uint64_t *bar) {
+  const int64_t r0 = (int64_t)t * TR;
+  const int rows = (int)min((int64_t)TR, a.n - r0);
+  const int rt = rows & ~7;
+  uint32_t bytes = 0;
+  for (int c = 0; c < a.ncol; ++c) bytes += (uint32_t)(rt * col_esz<QT>(a, c));
+  mbar_arrive_expect_tx(bar, bytes);
+  if (rt > 0) {
+    for (int c = 0; c < a.ncol; ++c) {
+      const int es = col_esz<QT>(a, c);
+      const char *src = (const char *)a.col[c] + r0 * es;
+      bulk_g2s(st.base + (size_t)c * TR * 8, src, (uint32_t)(rt * es), bar);
+    }
+  }
+}
+
+template <class QT>
+__device__ __forceinline__ void load_tail_row(const PassArgs &a, Stage st, int t, int r) {
+  const int64_t row = (int64_t)t * TR + r;
+  for (int c = 0; c < a.ncol; ++c) {
+    if (c >= a.qbase)
+      st.q<QT>(c)[r] = ((const QT *)a.col[c])[row];
+    else
+      st.d(c)[r] = ((const double *)a.col[c])[row];
+  }
+}
+
+template <class QT>
+__device__ __forceinline__ double ldv(Stage st, int c, int r, bool isq) {
+  return isq ? to_d<QT>(st.q<QT>(c)[r]) : st.d(c)[r];
+}
+
+// ----------------------------------------------------------- row programs
+
+// Shared coefficient block layout (doubles).
+constexpr int CO_ROT = 0;              // 4*(m-1) folded rotation coefficients
+constexpr int CO_ROT0 = 4 * MMAX;      // sig_0
+constexpr int CO_COEF = 4 * MMAX + 1;  // coef[0..k)
+constexpr int CO_COEF2 = 5 * MMAX + 1; // coef2[0..k-1)
+constexpr int CO_MISC = 6 * MMAX + 1;  // rcself, vscale
+constexpr int CO_SIZE = 6 * MMAX + 4;
+
+template <class QT>
+__device__ __forceinline__ void row_program(const PassArgs &a, Stage st, int t, int r,
+                                            const double *co) {
+  const int64_t row = (int64_t)t * TR + r;
+  switch (a.kind) {
+    case K_INIT: {
+      const double x = st.d(0)[r], g = st.d(1)[r];
+      const double f = g - x;
+      a.out_f[row] = f;
+      a.out_g[row] = g;
+      a.out_x[row] = g;
+      st.d(0)[r] = f;
+      break;
+    }
+    case K_A: {
+      double df;
+      if (a.step_mode) {
+        const double x = st.d(0)[r], g = st.d(1)[r], gp = st.d(2)[r], fp = st.d(3)[r];
+        const double f = g - x;
+        df = f - fp;
+        const double dg = g - gp;
+        ((QT *)a.out_dg)[row] = from_d<QT>(dg);
+        a.out_f[row] = f;
+        a.out_g[row] = g;
+        st.d(0)[r] = f;
+        st.d(1)[r] = df;
+      } else {
+        df = st.d(0)[r];
+      }
+      a.out_df[row] = df;
+      if (a.k == 0) ((QT *)a.out_q[0])[row] = from_d<QT>(df);
+      if (a.del) {
+        // QRDelete: sequential Givens rotations of adjacent columns; column
+        // j is final once rotation j has been applied.  Coefficients are
+        // folded with the stored columns' scales.
+        const int qb = a.qbase;
+        double carry = co[CO_ROT0] * to_d<QT>(st.q<QT>(qb)[r]);
+        for (int j = 0; j < a.m - 1; ++j) {
+          const double b = to_d<QT>(st.q<QT>(qb + j + 1)[r]);
+          const double *R = co + CO_ROT + 4 * j;
+          const double qj = R[0] * carry + R[1] * b;
+          carry = R[2] * carry + R[3] * b;
+          const QT qs = from_d<QT>(qj);
+          ((QT *)a.out_q[j])[row] = qs;
+          st.q<QT>(qb + j)[r] = qs;
+        }
+      }
+      break;
+    }
+    case K_PROJ: {
+      const int qb = a.qbase;
+      double v = st.d(0)[r];
+      if (a.orth == O_DCGS2 && (a.flags & 0x100u)) {
+        // DCGS-2: correct q_{k-1} against q_0..q_{k-2}, store it, then
+        // project v against the corrected factor.
+        const int kk = a.k - 1;
+        double qn = co[CO_MISC] * to_d<QT>(st.q<QT>(qb + kk)[r]);
+        for (int j = 0; j < kk; ++j) qn -= co[CO_COEF2 + j] * to_d<QT>(st.q<QT>(qb + j)[r]);
+        const QT qs = from_d<QT>(qn);
+        ((QT *)a.out_q[kk])[row] = qs;
+        st.q<QT>(qb + kk)[r] = qs;
+      }
+      for (int j = a.j0; j < a.k; ++j) v -= co[CO_COEF + j] * to_d<QT>(st.q<QT>(qb + j - a.j0)[r]);
+      ((QT *)a.out_q[a.k])[row] = from_d<QT>(v * co[CO_MISC + 1]);
+      st.d(0)[r] = v;
+      break;
+    }
+    case K_CGS2B: {
+      double y = st.d(0)[r];
+      for (int j = 0; j < a.k; ++j) y -= co[CO_COEF + j] * to_d<QT>(st.q<QT>(a.qbase + j)[r]);
+      a.out_df[row] = y;
+      st.d(0)[r] = y;
+      break;
+    }
+    case K_MGS: {
+      const double v = st.d(0)[r] - co[CO_COEF + a.jm - 1] * to_d<QT>(st.q<QT>(a.qbase)[r]);
+      a.out_df[row] = v;
+      st.d(0)[r] = v;
+      break;
+    }
+    case K_UPDATE: {
+      double xn = st.d(0)[r];
+      for (int i = 0; i < a.ng; ++i) xn -= co[CO_COEF + i] * to_d<QT>(st.q<QT>(a.qbase + i)[r]);
+      a.out_x[row] = xn;
+      if (a.stop_kind == 1) st.d(1)[r] = xn - st.d(1)[r];
+      break;
+    }
+    default:
+      break;
+  }
+}
+
+// ------------------------------------------------------- m x m epilogues
+//
+// The small dense part of each add runs in the last CTA of a pass, by warp
+// 0, on shared-memory copies of the m x m state (the stage buffers are free
+// once the tile loop has ended).  Layout of the scratch (doubles, ld = M):
+//   Rs[M*M], Ts[M*M], then vectors sig, rhs, rcol, gam, coef, s (M each).
+
+__device__ __forceinline__ double &RR(double *A, int j, int l) { return A[j * MMAX + l]; }
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+struct Epi {
+  int M;
+  double *R, *T, *sig, *rhs, *rcol, *gam, *coef, *s;
+  __device__ double &r(int j, int l) const { return R[j * M + l]; }
+  __device__ double &t(int j, int l) const { return T[j * M + l]; }
+};
+
+__host__ __device__ inline size_t epi_doubles(int M) { return (size_t)2 * M * M + 6 * (size_t)M + 8; }
+
+static __device__ Epi epi_layout(double *base, int M) {
+  Epi e;
+  e.M = M;
+  e.R = base;
+  e.T = e.R + M * M;
+  e.sig = e.T + M * M;
+  e.rhs = e.sig + M;
+  e.rcol = e.rhs + M;
+  e.gam = e.rcol + M;
+  e.coef = e.gam + M;
+  e.s = e.coef + M;
+  return e;
+}
+
+// Copy a ld-MMAX global matrix into a ld-M shared one (and back).
+static __device__ void mat_in(double *dst, const double *src, int M, int lane) {
+  for (int i = lane; i < M * M; i += 32) dst[i] = src[(i / M) * MMAX + (i % M)];
+  __syncwarp();
+}
+static __device__ void mat_out(double *dst, const double *src, int M, int lane) {
+  for (int i = lane; i < M * M; i += 32) dst[(i / M) * MMAX + (i % M)] = src[i];
+  for (int i = lane; i < MMAX * MMAX; i += 32)
+    if ((i / MMAX) >= M || (i % MMAX) >= M) dst[i] = 0.0;
+  __syncwarp();
+}
+static __device__ void vec_in(double *dst, const double *src, int n, int lane) {
+  for (int i = lane; i < n; i += 32) dst[i] = src[i];
+  __syncwarp();
+}
+static __device__ void vec_out(double *dst, const double *src, int n, int lane) {
+  for (int i = lane; i < n; i += 32) dst[i] = src[i];
+  __syncwarp();
+}
+
+// Back substitution with an upper-triangular R (ld M): x = R^{-1} b, n unknowns.
+static __device__ void backsolve(const Epi &e, const double *b, double *x, int n, int lane) {
+  for (int j = n - 1; j >= 0; --j) {
+    double p = 0.0;
+    for (int l = j + 1 + lane; l < n; l += 32) p += e.R[j * e.M + l] * x[l];
+    p = warp_sum(p);
+    if (lane == 0) x[j] = (b[j] - p) / e.R[j * e.M + j];
+    __syncwarp();
+  }
+}
+
+// Forward substitution with the unit-lower T (ld M): x = T^{-1} x in place.
+static __device__ void forward_unit(const Epi &e, double *x, int n, int lane) {
+  for (int j = 1; j < n; ++j) {
+    double p = 0.0;
+    for (int l = lane; l < j; l += 32) p += e.T[j * e.M + l] * x[l];
+    p = warp_sum(p);
+    if (lane == 0) x[j] -= p;
+    __syncwarp();
+  }
+}
+
+// Givens parameters of the next QRDelete, computed from R alone: the rotated
+// R, the per-row rotation coefficients folded with the stored columns'
+// scales, and (ICWY) the correction matrix rotated at the m x m level.
+// Runs when the history has just become full; overwrites e.R and e.T.
+static __device__ void prepare_delete(const PassArgs &a, DevState *S, const Epi &e, int lane) {
+  const int M = e.M;
+  const bool icwy_rot = (a.orth == O_ICWY) && !(a.flags & 0x2u);
+  // H = R without its first column (M x (M-1), upper Hessenberg), in place.
+  for (int j = 0; j < M; ++j) {
+    double v[2];
+    int cnt = 0;
+    for (int l = lane; l < M; l += 32) v[cnt++] = (l + 1 < M) ? e.r(j, l + 1) : 0.0;
+    __syncwarp();
+    cnt = 0;
+    for (int l = lane; l < M; l += 32) e.r(j, l) = v[cnt++];
+    __syncwarp();
+  }
+  if (icwy_rot) {
+    // Gram of the stored columns 0..M-2 from T = I + L (strictly-lower part
+    // kept in place, mirrored into the upper part); the delayed row of
+    // column M-1 is still unknown and is left as an identity row/column.
+    for (int i = lane; i < M * M; i += 32) {
+      const int j = i / M, l = i % M;
+      if (j < l) e.T[i] = (l < M - 1) ? e.t(l, j) : 0.0;
+    }
+    __syncwarp();
+    for (int i = lane; i < M * M; i += 32) {
+      const int j = i / M, l = i % M;
+      if (j == l) e.T[i] = 1.0;
+      else if (j > l && j == M - 1) e.T[i] = 0.0;
+    }
+    __syncwarp();
+  }
+  for (int j = 0; j + 1 < M; ++j) {
+    const double av = e.r(j, j), bv = e.r(j + 1, j);
+    const double rho = hypot(av, bv);
+    double c = 1.0, s = 0.0;
+    if (rho != 0.0) {
+      c = av / rho;
+      s = bv / rho;
+    }
+    __syncwarp();
+    for (int l = j + lane; l + 1 < M; l += 32) {
+      const double hj = e.r(j, l), hj1 = e.r(j + 1, l);
+      e.r(j, l) = c * hj + s * hj1;
+      e.r(j + 1, l) = -s * hj + c * hj1;
+    }
+    __syncwarp();
+    if (lane == 0) {
+      e.r(j + 1, j) = 0.0;
+      S->rot[4 * j + 0] = c;
+      S->rot[4 * j + 1] = s * e.sig[j + 1];
+      S->rot[4 * j + 2] = -s;
+      S->rot[4 * j + 3] = c * e.sig[j + 1];
+    }
+    if (icwy_rot) {
+      for (int i = lane; i < M; i += 32) {  // columns j, j+1
+        const double gj = e.t(i, j), gj1 = e.t(i, j + 1);
+        e.t(i, j) = c * gj + s * gj1;
+        e.t(i, j + 1) = -s * gj + c * gj1;
+      }
+      __syncwarp();
+      for (int l = lane; l < M; l += 32) {  // rows j, j+1
+        const double gj = e.t(j, l), gj1 = e.t(j + 1, l);
+        e.t(j, l) = c * gj + s * gj1;
+        e.t(j + 1, l) = -s * gj + c * gj1;
+      }
+    }
+    __syncwarp();
+  }
+  for (int l = lane; l < M; l += 32) e.r(M - 1, l) = 0.0;
+  __syncwarp();
+  mat_out(S->Rn, e.R, M, lane);
+  if (icwy_rot) {
+    // T' = I + strictly-lower Gram of the rotated columns 0..M-3; row M-2 is
+    // the delayed row that the next add computes.
+    for (int i = lane; i < M * M; i += 32) {
+      const int j = i / M, l = i % M;
+      double v = 0.0;
+      if (j == l && j < M - 1) v = 1.0;
+      else if (l < j && j <= M - 3) v = e.T[i];
+      e.T[i] = v;
+    }
+    __syncwarp();
+    mat_out(S->Tn, e.T, M, lane);
+  }
+  if (lane == 0) {
+    S->rot0 = e.sig[0];
+    S->pend_del = 1;
+  }
+  __syncwarp();
+}
+
+// Finish a QRAdd: diagonal entry, breakdown test, the least-squares solve of
+// Algorithm 2 (step mode) and gamma in dG slot order.  e holds R, T, sig,
+// rhs and rcol for the current add.
+static __device__ void finalize_add(const PassArgs &a, DevState *S, const Epi &e, double rho, double vf,
+                             double vscale, double qnf, int lane) {
+  const int k = a.k, m = a.m;
+  const double dfn = sqrt(S->st.dfnorm2);
+  const bool bd = !(rho > 0.0) || !isfinite(rho) || rho <= a.breakdown_tol * dfn;
+  if (bd) {
+    for (int j = lane; j < MMAX; j += 32) S->gphys[j] = 0.0;
+    if (lane == 0) {
+      S->st.rho = rho;
+      S->st.breakdown = 1;
+      S->st.cols = 0;
+      S->pend_del = 0;
+    }
+    __syncwarp();
+    return;
+  }
+  for (int l = lane; l < m; l += 32) e.r(k, l) = 0.0;
+  __syncwarp();
+  for (int j = lane; j < k; j += 32) e.r(j, k) = e.rcol[j];
+  if (lane == 0) {
+    e.r(k, k) = rho;
+    e.sig[k] = 1.0 / (rho * vscale);
+  }
+  if (a.orth == O_ICWY) {
+    for (int l = lane; l < m; l += 32) e.t(k, l) = (l == k) ? 1.0 : 0.0;
+  }
+  __syncwarp();
+  if (a.step_mode) {
+    if (lane == 0) {
+      e.rhs[k] = vf / rho;
+      if (a.orth == O_DCGS2 && (a.flags & 0x100u)) e.rhs[k - 1] = qnf;
+    }
+    __syncwarp();
+    backsolve(e, e.rhs, e.gam, k + 1, lane);
+    for (int j = lane; j < MMAX; j += 32) S->gphys[j] = 0.0;
+    __syncwarp();
+    for (int j = lane; j <= k; j += 32) S->gphys[(a.head_new + j) % m] = e.gam[j];
+    vec_out(S->rhs, e.rhs, k + 1, lane);
+    vec_out(S->gam, e.gam, k + 1, lane);
+  }
+  mat_out(S->R, e.R, m, lane);
+  if (a.orth == O_ICWY) mat_out(S->T, e.T, m, lane);
+  vec_out(S->sig, e.sig, k + 1, lane);
+  if (lane == 0) {
+    S->st.rho = rho;
+    S->st.breakdown = 0;
+    S->st.cols = k + 1;
+  }
+  __syncwarp();
+  if (k + 1 == m) prepare_delete(a, S, e, lane);
+}
+
+// Warp 0 of the last CTA.
+static __device__ void epilogue(const PassArgs &a, double *scratch, int lane) {
+  DevState *S = a.st;
+  const double *red = S->red;
+  const int k = a.k;
+  const int m = a.m;
+  Epi e = epi_layout(scratch, m > 0 ? m : 1);
+  switch (a.kind) {
+    case K_INIT: {
+      if (lane == 0) {
+        S->st.fnorm2 = red[0];
+        if (!isfinite(red[0])) S->st.status = DEV_ENONFINITE;
+      }
+      break;
+    }
+    case K_A: {
+      const int o = a.step_mode ? 1 : 0;
+      const double dfn2 = red[o];
+      const double fn2 = a.step_mode ? red[0] : 0.0;
+      if (lane == 0) {
+        if (a.step_mode) S->st.fnorm2 = fn2;
+        S->st.dfnorm2 = dfn2;
+      }
+      if (!isfinite(dfn2) || !isfinite(fn2)) {
+        for (int j = lane; j < MMAX; j += 32) S->gphys[j] = 0.0;
+        if (lane == 0) {
+          S->st.status = DEV_ENONFINITE;
+          S->st.breakdown = 1;
+          S->st.cols = 0;
+          S->pend_del = 0;
+        }
+        break;
+      }
+      // current state -> shared memory (after a delete: the pending rotated R/T)
+      mat_in(e.R, a.del ? S->Rn : S->R, m, lane);
+      if (a.orth == O_ICWY) mat_in(e.T, (a.del && !(a.flags & 0x2u)) ? S->Tn : S->T, m, lane);
+      vec_in(e.sig, S->sig, m, lane);
+      vec_in(e.rcol, S->rcol, m, lane);
+      if (a.del) {
+        for (int j = lane; j < k; j += 32) e.sig[j] = 1.0;
+        if (lane == 0) S->pend_del = 0;
+        __syncwarp();
+      }
+      if (k == 0) {
+        finalize_add(a, S, e, sqrt(dfn2), a.step_mode ? red[2] : 0.0, 1.0, 0.0, lane);
+        break;
+      }
+      if (a.step_mode)
+        for (int j = lane; j < k; j += 32) e.rhs[j] = e.sig[j] * red[a.off_rhs + j];
+      if (lane == 0) S->vscale = dfn2 > 0.0 ? 1.0 / sqrt(dfn2) : 1.0;
+      __syncwarp();
+      switch (a.orth) {
+        case O_MGS: {
+          if (lane == 0) {
+            const double r0 = e.sig[0] * red[a.off_r];
+            S->rcol[0] = r0;
+            S->coef[0] = r0 * e.sig[0];
+          }
+          break;
+        }
+        case O_ICWY: {
+          if ((a.flags & 0x2u) && a.del) {
+            // T refreshed from the Gram reduction of the rotated factor
+            for (int i = lane; i < m * m; i += 32) e.T[i] = ((i / m) == (i % m)) ? 1.0 : 0.0;
+            __syncwarp();
+            if (lane == 0) {
+              int g = 0;
+              for (int j = 1; j <= k - 2; ++j)
+                for (int l = 0; l < j; ++l) e.t(j, l) = red[a.off_gram + g++];
+            }
+            __syncwarp();
+          }
+          for (int l = lane; l < m; l += 32)
+            e.t(k - 1, l) = (l + 1 < k) ? e.sig[l] * e.sig[k - 1] * red[a.off_t + l]
+                                        : ((l == k - 1) ? 1.0 : 0.0);
+          for (int j = lane; j < k; j += 32) e.rcol[j] = e.sig[j] * red[a.off_r + j];
+          __syncwarp();
+          forward_unit(e, e.rcol, k, lane);
+          for (int j = lane; j < k; j += 32) e.coef[j] = e.sig[j] * e.rcol[j];
+          __syncwarp();
+          mat_out(S->T, e.T, m, lane);
+          vec_out(S->rcol, e.rcol, k, lane);
+          vec_out(S->coef, e.coef, k, lane);
+          break;
+        }
+        case O_CGS2: {
+          for (int j = lane; j < k; j += 32) {
+            const double sj = e.sig[j] * red[a.off_r + j];
+            S->s[j] = sj;
+            S->coef[j] = e.sig[j] * sj;
+          }
+          break;
+        }
+        default: {  // DCGS-2
+          for (int j = lane; j < k; j += 32) e.rcol[j] = e.sig[j] * red[a.off_r + j];
+          const bool reorth = (a.flags & 0x100u) != 0;
+          __syncwarp();
+          if (reorth) {
+            const double rkk = e.r(k - 1, k - 1);
+            const double sk = e.sig[k - 1];
+            for (int j = lane; j < k - 1; j += 32) {
+              const double sj = e.sig[j] * sk * red[a.off_s + j];
+              S->s[j] = sj;
+              e.r(j, k - 1) += (a.flags & 0x1u) ? rkk * sj : sj;
+              S->coef2[j] = sj * e.sig[j];
+            }
+            __syncwarp();
+            if (lane == 0) {
+              S->rcself = sk;
+              e.sig[k - 1] = 1.0;
+            }
+            __syncwarp();
+          }
+          for (int j = lane; j < k; j += 32) e.coef[j] = e.rcol[j] * e.sig[j];
+          __syncwarp();
+          vec_out(S->rcol, e.rcol, k, lane);
+          vec_out(S->coef, e.coef, k, lane);
+          if (lane == 0) S->reorth = reorth;
+          break;
+        }
+      }
+      __syncwarp();
+      mat_out(S->R, e.R, m, lane);
+      vec_out(S->sig, e.sig, m, lane);
+      if (a.step_mode) vec_out(S->rhs, e.rhs, k, lane);
+      break;
+    }
+    case K_CGS2B: {
+      for (int j = lane; j < k; j += 32) {
+        const double z = S->sig[j] * red[j];
+        S->rcol[j] = S->s[j] + z;
+        S->coef[j] = S->sig[j] * z;
+      }
+      break;
+    }
+    case K_MGS: {
+      if (lane == 0) {
+        const double r = S->sig[a.jm] * red[0];
+        S->rcol[a.jm] = r;
+        S->coef[a.jm] = r * S->sig[a.jm];
+      }
+      break;
+    }
+    case K_PROJ: {
+      const double vn2 = red[0];
+      const double vf = a.step_mode ? red[1] : 0.0;
+      const double qnf = (a.step_mode && a.orth == O_DCGS2 && (a.flags & 0x100u)) ? red[2] : 0.0;
+      mat_in(e.R, S->R, m, lane);
+      if (a.orth == O_ICWY) mat_in(e.T, S->T, m, lane);
+      vec_in(e.sig, S->sig, m, lane);
+      vec_in(e.rcol, S->rcol, m, lane);
+      vec_in(e.rhs, S->rhs, m, lane);
+      finalize_add(a, S, e, sqrt(vn2), vf, S->vscale, qnf, lane);
+      break;
+    }
+    case K_UPDATE: {
+      if (lane == 0) S->st.xdiff2 = red[0];
+      break;
+    }
+    case K_LSQ: {
+      const int c = a.c;
+      mat_in(e.R, S->R, m, lane);
+      for (int j = lane; j < c; j += 32) e.rhs[j] = S->sig[j] * red[j];
+      __syncwarp();
+      backsolve(e, e.rhs, e.gam, c, lane);
+      vec_out(S->rhs, e.rhs, c, lane);
+      vec_out(S->gam, e.gam, c, lane);
+      break;
+    }
+    case K_MDOT: {
+      for (int d = lane; d < a.ndots; d += 32) a.result_host_dev[d] = red[d];
+      break;
+    }
+    default:
+      break;
+  }
+  __syncwarp();
+}
+
+// ---------------------------------------------------------------- kernel
+
+template <class QT, int DPW>
+__global__ void __launch_bounds__(NT) pass_kernel(const __grid_constant__ PassArgs a, int nstages) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bars[STAGES];
+  __shared__ double co[CO_SIZE];
+  __shared__ uint8_t sda[NDOT_MAX], sdb[NDOT_MAX];
+  __shared__ int s_last;
+  __shared__ int s_err;
+
+  const int tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  const size_t stage_bytes = (size_t)a.ncol * TR * 8;
+  DevState *S = a.st;
+
+  // Per-pass coefficients from the device state (written by earlier passes).
+  for (int i = tid; i < CO_SIZE; i += NT) co[i] = 0.0;
+  for (int d = tid; d < a.ndots; d += NT) {
+    sda[d] = a.dot_a[d];
+    sdb[d] = a.dot_b[d];
+  }
+  if (tid == 0) s_err = 0;
+  __syncthreads();
+  if (a.kind == K_A && a.del) {
+    for (int i = tid; i < 4 * (a.m - 1); i += NT) co[CO_ROT + i] = S->rot[i];
+    if (tid == 0) co[CO_ROT0] = S->rot0;
+  } else if (a.kind == K_PROJ || a.kind == K_CGS2B || a.kind == K_MGS) {
+    for (int i = tid; i < a.k; i += NT) {
+      co[CO_COEF + i] = S->coef[i];
+      co[CO_COEF2 + i] = S->coef2[i];
+    }
+    if (tid == 0) {
+      co[CO_MISC] = S->rcself;
+      co[CO_MISC + 1] = S->vscale;
+    }
+  } else if (a.kind == K_UPDATE) {
+    for (int i = tid; i < a.ng; i += NT) co[CO_COEF + i] = S->gphys[a.pslot[i]];
+  }
+  if (tid == 0) {
+    for (int s = 0; s < nstages; ++s) mbar_init(&bars[s], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  if (tid == 0) {
+    for (int s = 0; s < nstages; ++s) {
+      const int t = blockIdx.x + s * gridDim.x;
+      if (t < a.ntiles) issue_tile<QT>(a, Stage{smem + s * stage_bytes}, t, &bars[s]);
+    }
+  }
+
+  double acc[DPW];
+#pragma unroll
+  for (int i = 0; i < DPW; ++i) acc[i] = 0.0;
+
+  int it = 0;
+  for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++it) {
+    const int s = it % nstages;
+    const uint32_t parity = (uint32_t)((it / nstages) & 1);
+    Stage st{smem + s * stage_bytes};
+    const int rows = (int)min((int64_t)TR, a.n - (int64_t)t * TR);
+    const int rt = rows & ~7;
+    if (!mbar_wait_bounded(&bars[s], parity)) s_err = 1;
+    __syncthreads();
+    if (s_err) break;
+    if (tid >= rt && tid < rows) load_tail_row<QT>(a, st, t, tid);
+    if (tid < rows) row_program<QT>(a, st, t, tid, co);
+    __syncthreads();
+    // dot phase: warp w owns dots w, w + NWARP, ...
+#pragma unroll
+    for (int i = 0; i < DPW; ++i) {
+      const int d = warp + NWARP * i;
+      if (d < a.ndots) {
+        const int ca = sda[d], cb = sdb[d];
+        const bool qa = ca >= a.qbase, qb = cb >= a.qbase;
+        double sum = 0.0;
+        for (int r = lane; r < rows; r += 32) sum += ldv<QT>(st, ca, r, qa) * ldv<QT>(st, cb, r, qb);
+        acc[i] += sum;
+      }
+    }
+    __syncthreads();
+    if (tid == 0) {
+      const int tn = t + nstages * gridDim.x;
+      if (tn < a.ntiles) {
+        fence_proxy_async();
+        issue_tile<QT>(a, st, tn, &bars[s]);
+      }
+    }
+  }
+
+  if (s_err) {
+    // A copy did not complete in time: record it, give the copies still in
+    // flight a bounded chance to land, and leave without touching the state.
+    if (tid == 0) {
+      atomicExch(&S->st.status, DEV_ETIMEOUT);
+      for (int s = 0; s < nstages; ++s) (void)mbar_wait_bounded(&bars[s], 0);
+    }
+    return;
+  }
+  const bool has_epilogue = a.ndots > 0 || a.kind == K_A || a.kind == K_PROJ;
+  if (!has_epilogue) return;
+
+  // Per-CTA partial sums (warp butterfly, fixed order).
+#pragma unroll
+  for (int i = 0; i < DPW; ++i) {
+    const int d = warp + NWARP * i;
+    double v = acc[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0 && d < a.ndots) a.partials[(size_t)blockIdx.x * NDOT_MAX + d] = v;
+  }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) {
+    const unsigned tk = atomicAdd(&S->ticket, 1u);
+    s_last = (tk == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  // Last CTA: finish the reduction in CTA order (bit-reproducible).
+  for (int d = tid; d < a.ndots; d += NT) {
+    double v = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) v += __ldcg(&a.partials[(size_t)b * NDOT_MAX + d]);
+    S->red[d] = v;
+  }
+  __threadfence();
+  __syncthreads();
+  if (warp == 0) {
+    epilogue(a, (double *)smem, lane);
+    if (lane == 0) S->ticket = 0;
+    __threadfence();
+  }
+}
+
+// ------------------------------------------------------------ host launch
+
+template <class QT, int DPW>
+static cudaError_t launch_t(const PassArgs &a, int grid, size_t smem, int nstages,
+                            cudaStream_t stream) {
+  static bool attr_set = false;  // per instantiation
+  auto kern = pass_kernel<QT, DPW>;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         227 * 1024 - 8 * 1024);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  kern<<<grid, NT, smem, stream>>>(a, nstages);
+  return cudaGetLastError();
+}
+
+template <class QT, int DPW>
+static int occupancy_t(size_t smem) {
+  int nb = 0;
+  auto kern = pass_kernel<QT, DPW>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024 - 8 * 1024);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, NT, smem) != cudaSuccess) return 1;
+  return nb < 1 ? 1 : nb;
+}
+
+template <class QT>
+static inline cudaError_t launch_q(const PassArgs &a, int nsm, int *grid_out, cudaStream_t stream) {
+  const size_t stage = (size_t)a.ncol * TR * 8;
+  const size_t budget = 227 * 1024 - 8 * 1024;
+  int nstages = (stage * STAGES <= budget) ? STAGES : 1;
+  size_t smem = stage * nstages;
+  const size_t epi = epi_doubles(a.m > 0 ? a.m : 1) * sizeof(double);
+  if (smem < epi) smem = epi;
+  if (smem > budget) return cudaErrorInvalidConfiguration;
+  int occ;
+  const int dpw_need = (a.ndots + NWARP - 1) / NWARP;
+  if (dpw_need <= 1) occ = occupancy_t<QT, 1>(smem);
+  else if (dpw_need <= 4) occ = occupancy_t<QT, 4>(smem);
+  else if (dpw_need <= 16) occ = occupancy_t<QT, 16>(smem);
+  else occ = occupancy_t<QT, 32>(smem);
+  int grid = nsm * occ;
+  if (grid > a.ntiles) grid = a.ntiles;
+  if (grid < 1) grid = 1;
+  *grid_out = grid;
+  if (dpw_need <= 1) return launch_t<QT, 1>(a, grid, smem, nstages, stream);
+  if (dpw_need <= 4) return launch_t<QT, 4>(a, grid, smem, nstages, stream);
+  if (dpw_need <= 16) return launch_t<QT, 16>(a, grid, smem, nstages, stream);
+  return launch_t<QT, 32>(a, grid, smem, nstages, stream);
+}
+
+}  // namespace aa
