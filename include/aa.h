@@ -161,6 +161,30 @@ int aa_pass_times(const aa_ctx *ctx, double *ms_out, int64_t *count_out);
 int aa_mdot(const double *A_dev, int64_t lda, int k, const double *V_dev, int64_t ldv, int nv,
             int64_t n, double *out_host, void *stream);
 
+/* Allocation-free variant of aa_mdot.  The paper has no counterpart: this
+ * entry point exists for callers that must not allocate device memory --
+ * frameworks whose own pool owns all device memory, processes running close
+ * to the device's memory limit, and latency-critical loops in which
+ * cudaMalloc/cudaFree would synchronize the device.  It computes the same
+ * products as aa_mdot with the same deterministic reduction, but its
+ * reduction scratch is a file-scope device array of about 0.76 MB (the
+ * reduction state plus 304 x 256 partial sums) that every GPU which loads
+ * the library holds until the process exits; it calls no cudaMalloc,
+ * cudaFree or other allocating routine.
+ *  - Sizes: same limits as aa_mdot (k*nv <= 256, k + nv <= 70, lda, ldv >= n,
+ *    columns 16-byte aligned); larger requests return AA_EINVAL.
+ *  - Output: out_dev (device, k*nv FP64, out_dev[j*nv + v]) is written on
+ *    `stream`; the call does not synchronize.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress, with that device current); make that first call
+ *    before any stream capture.
+ *  - Every call shares the one array and leaves its contents behind; the
+ *    call clears what must start at zero itself.  Calls whose work overlaps
+ *    on the GPU (for example on two streams) race on the array: serialize
+ *    them. */
+int aa_mdot_noalloc(const double *A_dev, int64_t lda, int k, const double *V_dev, int64_t ldv,
+                    int nv, int64_t n, double *out_dev, void *stream);
+
 /* ---------------------------------------------------------- test problems
  * Built-in fixed-point maps (aa_g_fn-compatible) for the seeded stencil
  * workloads.  `user` points to the matching parameter struct; b/src are

@@ -89,6 +89,8 @@ def lib():
         L.aa_pass_times.argtypes = [C.c_void_p, _dp, C.POINTER(C.c_int64)]
         L.aa_mdot.argtypes = [C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_int64, C.c_int,
                               C.c_int64, _dp, C.c_void_p]
+        L.aa_mdot_noalloc.argtypes = [C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_int64,
+                                      C.c_int, C.c_int64, C.c_void_p, C.c_void_p]
         for nm in ("aa_g_jacobi2d", "aa_g_jacobi3d", "aa_g_bratu2d"):
             getattr(L, nm).argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]
         L.aa_last_error.restype = C.c_char_p
@@ -215,3 +217,14 @@ def mdot(A, V):
     _check(lib().aa_mdot(_ptr(A), A.stride(0), k, _ptr(V), V.stride(0), nv, n,
                          out.ctypes.data_as(_dp), _stream()))
     return out.reshape(k, nv)
+
+
+def mdot_noalloc(A, V, out):
+    """aa_mdot_noalloc: A^T V into the FP64 CUDA tensor out (k*nv), no allocation."""
+    k, n = A.shape
+    nv = V.shape[0]
+    rc = lib().aa_mdot_noalloc(_ptr(A), A.stride(0), k, _ptr(V), V.stride(0), nv, n, _ptr(out),
+                               _stream())
+    if rc != AA_OK:
+        raise AAError(rc, "aa_mdot_noalloc failed")
+    return out
