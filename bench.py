@@ -46,6 +46,8 @@ def parse():
     p.add_argument("--orth", default="icwy", choices=["mgs", "icwy", "cgs2", "dcgs2"])
     p.add_argument("--m", type=int, default=20)
     p.add_argument("--storage", default="fp64", choices=["fp64", "fp32", "bf16"])
+    p.add_argument("--fp32-dots", action="store_true",
+                   help="FP64 storage with dot products on the FP32 pipe (AA_FLAG_FP32_DOTS)")
     p.add_argument("--nz", type=int, default=NZ)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
@@ -59,6 +61,22 @@ def dist_setup():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def max_over_ranks(ms: float, device=None) -> float:
+    """Max of a per-rank time over the process group (identity without one)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(steps: int, world: int, ms_max: float) -> float:
+    """Whole-job rate: iterations of all replicas over the slowest rank's time."""
+    return steps * world / (ms_max * 1e-3)
 
 
 def measured_peaks():
@@ -193,7 +211,8 @@ def run_ours(args, ws, rank, local):
     Pp = aa.C.cast(aa.C.pointer(P), aa.C.c_void_p)
     stream = torch.cuda.current_stream()
     sp = stream.cuda_stream
-    A = aa.Anderson(n, args.m, args.orth, args.storage, flags=aa.FLAG_TIMING, max_iters=10**6)
+    flags = aa.FLAG_TIMING | (aa.FLAG_FP32_DOTS if args.fp32_dots else 0)
+    A = aa.Anderson(n, args.m, args.orth, args.storage, flags=flags, max_iters=10**6)
     x = torch.zeros(n, dtype=torch.float64, device=dev)
     xn = torch.empty_like(x)
     g = torch.empty_like(x)
@@ -229,12 +248,7 @@ def run_ours(args, ws, rank, local):
     e1.record(stream)
     torch.cuda.synchronize()
     ck = clocks.stop()
-    ms = e0.elapsed_time(e1)
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), dev)
     st1 = A.stats()
     pt1 = A.pass_times()
     launches = (st1["launches"] - st0["launches"]) + args.steps  # + one G kernel per step
@@ -294,7 +308,7 @@ def run_ours(args, ws, rank, local):
         dist.destroy_process_group()
     if rank != 0:
         return None
-    value = args.steps * ws / (ms * 1e-3)
+    value = job_rate(args.steps, ws, ms)
     line = {
         "metric": f"AA iterations/s (3D 7-pt weighted Jacobi, n=406^3~2^26, m={args.m}, "
                   f"{args.orth.upper()})",
@@ -307,11 +321,13 @@ def run_ours(args, ws, rank, local):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64" if args.storage == "fp64" else f"f64 ({args.storage} history storage)",
+        "dtype": ("f64" + (" (FP32-pipe dot products)" if args.fp32_dots else ""))
+                 if args.storage == "fp64" else f"f64 ({args.storage} history storage)",
         "data": "synthetic (seeded SplitMix64 b ~ U(-1,1), x0 = 0)",
         "config": {"workload": f"AA({args.m}) {args.orth} on 3D 7-pt weighted Jacobi "
                                f"{nx}x{ny}x{nz}, recycle iterations",
                    "n": n, "m": args.m, "orth": args.orth, "storage": args.storage,
+                   "fp32_dots": bool(args.fp32_dots),
                    "parallelism": f"replicas x{ws}",
                    "l2": "inputs larger than L2 (history %.1f GB per replica)"
                          % (2 * n * args.m * esz / 1e9),

@@ -60,6 +60,10 @@ typedef enum { AA_STORE_FP64 = 0, AA_STORE_FP32 = 1, AA_STORE_BF16 = 2 } aa_stor
                                       the rotated Q (fused into the first pass, k <= 24) instead
                                       of rotating T at the m x m level */
 #define AA_FLAG_TIMING 0x4u        /* record CUDA events around every pass (aa_pass_times) */
+#define AA_FLAG_FP32_DOTS 0x8u     /* FP64 storage: dot products on the FP32 pipe from (hi, lo)
+                                      splits of the FP64 operands (error <= 2^-45 sum|a_i b_i|
+                                      per tile), accumulated in FP64 across tiles; updates of
+                                      Q, v and x stay FP64 */
 
 typedef struct aa_config {
   int64_t n;          /* vector length, >= 1 */
@@ -202,6 +206,48 @@ typedef struct aa_bratu2d {   /* nonlinear Jacobi for -Lap u = lambda e^u + src,
 int aa_g_jacobi2d(const double *x_dev, double *gx_dev, int64_t n, void *stream, void *user);
 int aa_g_jacobi3d(const double *x_dev, double *gx_dev, int64_t n, void *stream, void *user);
 int aa_g_bratu2d(const double *x_dev, double *gx_dev, int64_t n, void *stream, void *user);
+
+/* ------------------------------------------------------------ batched form
+ * Many independent AA(m) solves of the 2D Bratu nonlinear-Jacobi map
+ * (Sec. 5.2), u <- (sum of neighbours + h^2 (lambda e^u + src)) / 4 on
+ * s x s grids, h = 1/(s+1), zero boundary, in ONE persistent kernel launch
+ * (captured in a CUDA graph): each CTA pops the next solve from a queue
+ * (largest first) and runs the whole Anderson loop with ICWY QR updates
+ * (Algorithm 4) and block-level reductions.  Q and dG are stored in FP32,
+ * x/G(x)/f in FP64, R, T and gamma in FP64.  Stop: ||G(x_i) - x_i||_2 /
+ * ||G(0)||_2 < tol, or max_iters. */
+typedef struct aa_batch_desc {
+  int32_t count;          /* number of solves, >= 1 */
+  const int64_t *side;    /* host, count entries: grid side s_i (n_i = s_i^2), 1..46340 */
+  const double *lambda;   /* host, count entries */
+  const double *src_host; /* host, sum n_i values (solve i's block in input order), or NULL */
+  int32_t m;              /* history depth 1..16 */
+  double tol;             /* default 1e-8 when <= 0 */
+  int32_t max_iters;      /* default 100000 when <= 0 */
+  int32_t block, ctas_per_sm;  /* launch shape hints (aa_batch_solve takes them explicitly) */
+} aa_batch_desc;
+
+typedef struct aa_batch aa_batch;
+
+/* Allocates the arena (about 120 bytes per unknown for m = 10) and uploads
+ * the per-solve parameters.  AA_EINVAL / AA_ENOMEM. */
+int aa_batch_create(const aa_batch_desc *desc, aa_batch **out);
+void aa_batch_destroy(aa_batch *b);
+/* Optional initial guesses (host, sum n_i values in input order); NULL
+ * returns to x_0 = 0.  A solve whose ||G(x_0) - x_0|| is not below
+ * ||G(0)|| restarts from x_0 = 0 (reported per solve). */
+int aa_batch_set_x0(aa_batch *b, const double *x0_host);
+/* Runs every solve: one persistent launch of `block` threads (128, 256 or
+ * 512) x ctas_per_sm (1..4) CTAs per SM on `stream`; *ms_out (if not NULL)
+ * receives its CUDA-event time.  Synchronizes. */
+int aa_batch_solve(aa_batch *b, int block, int ctas_per_sm, void *stream, double *ms_out);
+/* Per-solve iterations, final ||f||/||G(0)|| and status (0 converged, 1 cap
+ * reached, AA_ENONFINITE) in input order; any pointer may be NULL. */
+int aa_batch_results(aa_batch *b, int32_t *iters, double *resid, int32_t *status);
+/* Solution of solve idx (host, n_idx doubles). */
+int aa_batch_solution(aa_batch *b, int idx, double *x_host);
+/* Total arena rows (sum of n_i rounded up to 64 each). */
+int64_t aa_batch_rows(const aa_batch *b);
 
 /* Message for the last error on this thread. */
 const char *aa_last_error(void);

@@ -21,6 +21,7 @@ STORAGE = {"fp64": 0, "fp32": 1, "bf16": 2}
 FLAG_DCGS2_SCALED = 0x1
 FLAG_ICWY_GRAM = 0x2
 FLAG_TIMING = 0x4
+FLAG_FP32_DOTS = 0x8
 PASS_KINDS = ["init", "A", "proj", "cgs2b", "mgs", "update", "lsq", "mdot"]
 
 AA_OK, AA_NOTCONVERGED = 0, 1
@@ -228,3 +229,90 @@ def mdot_noalloc(A, V, out):
     if rc != AA_OK:
         raise AAError(rc, "aa_mdot_noalloc failed")
     return out
+
+
+class BatchDesc(C.Structure):
+    _fields_ = [("count", C.c_int32), ("side", C.POINTER(C.c_int64)), ("lam", _dp),
+                ("src_host", _dp), ("m", C.c_int32), ("tol", C.c_double),
+                ("max_iters", C.c_int32), ("block", C.c_int32), ("ctas_per_sm", C.c_int32)]
+
+
+def _batch_lib():
+    L = lib()
+    if not getattr(L, "_batch_ready", False):
+        L.aa_batch_create.argtypes = [C.POINTER(BatchDesc), C.POINTER(C.c_void_p)]
+        L.aa_batch_destroy.argtypes = [C.c_void_p]
+        L.aa_batch_set_x0.argtypes = [C.c_void_p, _dp]
+        L.aa_batch_solve.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, _dp]
+        L.aa_batch_results.argtypes = [C.c_void_p, C.POINTER(C.c_int32), _dp, C.POINTER(C.c_int32)]
+        L.aa_batch_solution.argtypes = [C.c_void_p, C.c_int, _dp]
+        L.aa_batch_rows.argtypes = [C.c_void_p]
+        L.aa_batch_rows.restype = C.c_int64
+        L._batch_ready = True
+    return L
+
+
+class Batch:
+    """Many independent AA(m) Bratu solves in one persistent launch (aa_batch_*)."""
+
+    def __init__(self, sides, lams, *, m: int = 10, tol: float = 1e-8, max_iters: int = 100000,
+                 src=None):
+        import numpy as np
+        L = _batch_lib()
+        self.sides = np.ascontiguousarray(sides, dtype=np.int64)
+        self.lams = np.ascontiguousarray(lams, dtype=np.float64)
+        self.count = len(self.sides)
+        self._src = None if src is None else np.ascontiguousarray(src, dtype=np.float64)
+        d = BatchDesc()
+        d.count = self.count
+        d.side = self.sides.ctypes.data_as(C.POINTER(C.c_int64))
+        d.lam = self.lams.ctypes.data_as(_dp)
+        d.src_host = self._src.ctypes.data_as(_dp) if self._src is not None else None
+        d.m, d.tol, d.max_iters = int(m), float(tol), int(max_iters)
+        h = C.c_void_p()
+        _check(L.aa_batch_create(C.byref(d), C.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _batch_lib().aa_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_x0(self, x0=None):
+        import numpy as np
+        p = None
+        if x0 is not None:
+            self._x0 = np.ascontiguousarray(x0, dtype=np.float64)
+            p = self._x0.ctypes.data_as(_dp)
+        _check(_batch_lib().aa_batch_set_x0(self._h, p))
+
+    def solve(self, block: int = 256, ctas_per_sm: int = 1) -> float:
+        ms = C.c_double(0.0)
+        _check(_batch_lib().aa_batch_solve(self._h, int(block), int(ctas_per_sm), _stream(),
+                                           C.byref(ms)))
+        return ms.value
+
+    def results(self):
+        import numpy as np
+        it = np.zeros(self.count, dtype=np.int32)
+        rs = np.zeros(self.count)
+        stt = np.zeros(self.count, dtype=np.int32)
+        _check(_batch_lib().aa_batch_results(self._h, it.ctypes.data_as(C.POINTER(C.c_int32)),
+                                             rs.ctypes.data_as(_dp),
+                                             stt.ctypes.data_as(C.POINTER(C.c_int32))))
+        return it, rs, stt
+
+    def solution(self, i: int):
+        import numpy as np
+        x = np.zeros(int(self.sides[i]) ** 2)
+        _check(_batch_lib().aa_batch_solution(self._h, int(i), x.ctypes.data_as(_dp)))
+        return x
+
+    def rows(self) -> int:
+        return int(_batch_lib().aa_batch_rows(self._h))

@@ -253,6 +253,8 @@ static void base_args(aa_ctx *c, PassArgs &a, int kind) {
 static void add_dot(PassArgs &a, int x, int y) {
   a.dot_a[a.ndots] = (uint8_t)x;
   a.dot_b[a.ndots] = (uint8_t)y;
+  a.dotcols[x >> 6] |= 1ull << (x & 63);
+  a.dotcols[y >> 6] |= 1ull << (y & 63);
   a.ndots++;
 }
 

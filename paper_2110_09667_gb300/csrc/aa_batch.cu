@@ -1,0 +1,760 @@
+// aa_batch.cu -- many independent Anderson solves in one persistent launch.
+//
+// Workload: nonlinear-Jacobi fixed points of the 2D Bratu problem
+// (Sec. 5.2 of the paper) on s x s grids of different sizes,
+//   G(u)_p = (sum of the 4 neighbours + h^2 (lambda e^{u_p} + src_p)) / 4,
+// h = 1/(s+1), zero boundary, each solved by AA(m) with ICWY QR updates
+// (Algorithm 4; the variant the paper recommends on GPUs).
+//
+// Design: a persistent grid; each CTA pops the next solve from an atomic
+// queue (solves sorted largest first for load balance) and runs the whole
+// Anderson loop for it with block-level reductions (fixed order, so results
+// are bit-reproducible), then pops the next one.  Per iteration: pass A
+// evaluates G (the stencil reads x with its halo), forms f, Delta f, Delta g,
+// applies the QRDelete rotation and accumulates the first block of dot
+// products; warp 0 updates R and T; the projection pass forms the new
+// column; warp 0 solves for gamma; the update pass writes x_{i+1}.
+// Q and dG are stored in FP32 (the precision form) and every operation on
+// them runs on the FP32/INT pipes (aa_df.cuh); x, G(x), f, Delta f stay FP64,
+// and R, T, gamma are FP64.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <numeric>
+#include <vector>
+
+#include "../../include/aa.h"
+#include "aa_df.cuh"
+
+namespace {
+
+using aa::F2;
+
+constexpr int BM = 16;             // largest history depth of the batched form
+constexpr int BNDOT = 3 + 3 * BM;  // dot products of pass A at most
+
+struct Solve {
+  int64_t off;     // first row in the arena
+  int32_t s;       // grid side (n = s*s)
+  int32_t orig;    // index in the caller's order
+  double lambda;
+  double scale;    // ||G(0)||_2, the stopping scale (independent of x_0)
+};
+
+struct Result {
+  int32_t iters;     // iterations taken (x_0 is iterate 0)
+  int32_t status;    // 0 converged, 1 iteration cap reached, AA_ENONFINITE
+  double resid;      // ||f||/||G(0)|| at exit
+  int32_t fallback;  // 1 if the given x_0 was replaced by 0
+  int32_t pad;
+};
+
+struct BArgs {
+  const Solve *solves;
+  Result *res;
+  int count;
+  int m;
+  int max_iters;
+  double tol;
+  double breakdown_tol;
+  double *X0, *X1, *GP, *FP, *DF;  // FP64 vectors (arena rows)
+  float *Q, *DG;                    // m slots of N floats each
+  int64_t N;                        // arena rows
+  const double *src;                // optional source term (arena rows) or null
+  int warm;                         // x_0 given: fall back to 0 if ||f_0|| >= ||G(0)||
+  unsigned *queue;                  // next solve
+};
+
+// ---------------------------------------------------------------- state
+
+struct SState {
+  double R[BM * BM], T[BM * BM], Rn[BM * BM], Tn[BM * BM];
+  double sig[BM], rhs[BM], rcol[BM], coef[BM], gam[BM], gphys[BM];
+  double rot[4 * BM];
+  double red[BNDOT];
+  double scale, vscale, fn2, dfn2;
+  int c, head, pend, done, status, restarts, it, solve, fallback;
+  unsigned gmask;
+};
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block reduction of nd values per thread into st.red (fixed order).
+template <int NT>
+__device__ void block_reduce(double *vals, int nd, double *wbuf, SState &st) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int NW = NT / 32;
+  for (int d = 0; d < nd; ++d) {
+    const double v = warp_sum_d(vals[d]);
+    if (lane == 0) wbuf[warp * BNDOT + d] = v;
+  }
+  __syncthreads();
+  for (int d = threadIdx.x; d < nd; d += NT) {
+    double v = 0.0;
+    for (int w = 0; w < NW; ++w) v += wbuf[w * BNDOT + d];
+    st.red[d] = v;
+  }
+  __syncthreads();
+}
+
+// Warp 0: Givens parameters of the next QRDelete from R alone, in the scaled
+// two-multiply-add form, plus the rotated R and ICWY's rotated T (as in the
+// single-solve path).
+__device__ void prepare_delete_b(SState &st, int M, int lane) {
+  if (lane == 0) {
+    for (int j = 0; j < M; ++j)
+      for (int l = 0; l < M; ++l) st.Rn[j * BM + l] = (l + 1 < M) ? st.R[j * BM + l + 1] : 0.0;
+    for (int j = 0; j < M; ++j)
+      for (int l = 0; l < M; ++l) {
+        double g = (j == l) ? 1.0 : 0.0;
+        if (j != l && j < M - 1 && l < M - 1) g = (j > l) ? st.T[j * BM + l] : st.T[l * BM + j];
+        st.Tn[j * BM + l] = g;
+      }
+    double tau = st.sig[0];
+    for (int j = 0; j + 1 < M; ++j) {
+      const double av = st.Rn[j * BM + j], bv = st.Rn[(j + 1) * BM + j];
+      const double rho = hypot(av, bv);
+      double c = 1.0, s = 0.0;
+      if (rho != 0.0) {
+        c = av / rho;
+        s = bv / rho;
+      }
+      for (int l = j; l + 1 < M; ++l) {
+        const double hj = st.Rn[j * BM + l], hj1 = st.Rn[(j + 1) * BM + l];
+        st.Rn[j * BM + l] = c * hj + s * hj1;
+        st.Rn[(j + 1) * BM + l] = -s * hj + c * hj1;
+      }
+      st.Rn[(j + 1) * BM + j] = 0.0;
+      for (int i = 0; i < M; ++i) {
+        const double gj = st.Tn[i * BM + j], gj1 = st.Tn[i * BM + j + 1];
+        st.Tn[i * BM + j] = c * gj + s * gj1;
+        st.Tn[i * BM + j + 1] = -s * gj + c * gj1;
+      }
+      for (int l = 0; l < M; ++l) {
+        const double gj = st.Tn[j * BM + l], gj1 = st.Tn[(j + 1) * BM + l];
+        st.Tn[j * BM + l] = c * gj + s * gj1;
+        st.Tn[(j + 1) * BM + l] = -s * gj + c * gj1;
+      }
+      const double sj1 = st.sig[j + 1];
+      double k1, k2, sout, type;
+      if (fabs(c) >= fabs(s)) {
+        k1 = s * sj1 / (c * tau);
+        k2 = -s * tau / (c * sj1);
+        sout = c * tau;
+        tau = c * sj1;
+        type = 1.0;
+      } else {
+        k1 = c * tau / (s * sj1);
+        k2 = -c * sj1 / (s * tau);
+        sout = s * sj1;
+        tau = -s * tau;
+        type = 0.0;
+      }
+      st.rot[4 * j] = k1;
+      st.rot[4 * j + 1] = k2;
+      st.rot[4 * j + 2] = type;
+      st.rot[4 * j + 3] = sout;
+    }
+    for (int l = 0; l < M; ++l) st.Rn[(M - 1) * BM + l] = 0.0;
+    for (int j = 0; j < M; ++j)
+      for (int l = 0; l < M; ++l) {
+        double v = 0.0;
+        if (j == l && j < M - 1) v = 1.0;
+        else if (l < j && j <= M - 3) v = st.Tn[j * BM + l];
+        st.Tn[j * BM + l] = v;
+      }
+    st.pend = 1;
+  }
+  __syncwarp();
+}
+
+// Warp 0: finish an add (new diagonal, breakdown test, gamma).
+__device__ void finalize_b(SState &st, int m, int k, double rho, double vf, double vscale,
+                           int head_new, double bd_tol, int lane) {
+  if (lane == 0) {
+    const bool bd = !(rho > 0.0) || !isfinite(rho) || rho <= bd_tol * sqrt(st.dfn2);
+    if (bd) {
+      for (int j = 0; j < BM; ++j) st.gphys[j] = 0.0;
+      st.c = 0;
+      st.head = 0;
+      st.pend = 0;
+      st.restarts++;
+    } else {
+      for (int l = 0; l < m; ++l) st.R[k * BM + l] = 0.0;
+      for (int j = 0; j < k; ++j) st.R[j * BM + k] = st.rcol[j];
+      st.R[k * BM + k] = rho;
+      st.sig[k] = 1.0 / (rho * vscale);
+      for (int l = 0; l < m; ++l) st.T[k * BM + l] = (l == k) ? 1.0 : 0.0;
+      st.rhs[k] = vf / rho;
+      for (int j = k; j >= 0; --j) {
+        double s = st.rhs[j];
+        for (int l = j + 1; l <= k; ++l) s -= st.R[j * BM + l] * st.gam[l];
+        st.gam[j] = s / st.R[j * BM + j];
+      }
+      for (int j = 0; j < BM; ++j) st.gphys[j] = 0.0;
+      for (int j = 0; j <= k; ++j) st.gphys[(head_new + j) % m] = st.gam[j];
+      st.c = k + 1;
+      st.head = head_new;
+    }
+  }
+  __syncwarp();
+  if (st.c == m && st.pend == 0) prepare_delete_b(st, m, lane);
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT) batch_kernel(BArgs a) {
+  __shared__ SState st;
+  __shared__ double wbuf[(NT / 32) * BNDOT];
+  __shared__ float cfr[4 * BM], cfc[2 * BM], cfg[2 * BM], cfv[2];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int m = a.m;
+
+  for (;;) {
+    if (tid == 0) st.solve = (int)atomicAdd(a.queue, 1u);
+    __syncthreads();
+    const int si = st.solve;
+    if (si >= a.count) return;
+    const Solve S = a.solves[si];
+    const int s = S.s;
+    const int64_t n = (int64_t)s * s, off = S.off;
+    const double h = 1.0 / (double)(s + 1), h2 = h * h, lam = S.lambda;
+    if (tid == 0) {
+      st.c = 0;
+      st.head = 0;
+      st.pend = 0;
+      st.done = 0;
+      st.status = 1;
+      st.restarts = 0;
+      st.it = 0;
+      st.fallback = 0;
+      st.scale = S.scale;
+      for (int i = 0; i < BM * BM; ++i) st.R[i] = st.T[i] = 0.0;
+    }
+    __syncthreads();
+    double *Xc = a.X0 + off, *Xn = a.X1 + off;
+    double *GP = a.GP + off, *FP = a.FP + off, *DF = a.DF + off;
+    const double *src = a.src ? a.src + off : nullptr;
+    int it = 0;
+    for (;; ++it) {
+      const int c = st.c;
+      const bool del = (it > 0) && (c == m);
+      const int k = (it == 0) ? 0 : (del ? m - 1 : c);
+      const int head_new = del ? (st.head + 1) % m : st.head;
+      const int dg_slot = del ? st.head : (st.head + c) % m;
+      // ---- pass A: G, differences, rotation, first dot block
+      if (del) {
+        for (int j = tid; j < m - 1; j += NT) {
+          const F2 k1 = aa::d2f2(st.rot[4 * j]), k2 = aa::d2f2(st.rot[4 * j + 1]);
+          cfr[4 * j] = k1.h;
+          cfr[4 * j + 1] = k1.l;
+          cfr[4 * j + 2] = k2.h;
+          cfr[4 * j + 3] = k2.l;
+        }
+        __syncthreads();
+      }
+      const int nd = (it == 0) ? 1 : 3 + 3 * k - (k > 0 ? 1 : 0);
+      float aS[BNDOT], aC[BNDOT];
+#pragma unroll
+      for (int d = 0; d < BNDOT; ++d) aS[d] = aC[d] = 0.f;
+      for (int64_t r = tid; r < n; r += NT) {
+        const int64_t j = r / s, i = r - j * s;
+        const double x = Xc[r];
+        const double w = i > 0 ? Xc[r - 1] : 0.0;
+        const double e = i < s - 1 ? Xc[r + 1] : 0.0;
+        const double so = j > 0 ? Xc[r - s] : 0.0;
+        const double no = j < s - 1 ? Xc[r + s] : 0.0;
+        const double rhs = lam * exp(x) + (src ? src[r] : 0.0);
+        const double g = ((w + e) + (so + no) + h2 * rhs) / 4.0;
+        const double f = g - x;
+        const F2 f2 = aa::d2f2(f);
+        float p, q;
+        aa::prod_ff(f2, f2, p, q);
+        aa::acc_add(aS[0], aC[0], p, q);
+        if (it == 0) {
+          FP[r] = f;
+          GP[r] = g;
+          continue;
+        }
+        const double df = f - FP[r], dg = g - GP[r];
+        a.DG[(int64_t)dg_slot * a.N + off + r] = aa::d2f_rn(dg);
+        DF[r] = df;
+        FP[r] = f;
+        GP[r] = g;
+        const F2 d2 = aa::d2f2(df);
+        aa::prod_ff(d2, d2, p, q);
+        aa::acc_add(aS[1], aC[1], p, q);
+        aa::prod_ff(d2, f2, p, q);
+        aa::acc_add(aS[2], aC[2], p, q);
+        if (k == 0) a.Q[off + r] = aa::d2f_rn(df);
+        float qv[BM];
+#pragma unroll
+        for (int jj = 0; jj < BM; ++jj)
+          if (jj < c) qv[jj] = a.Q[(int64_t)jj * a.N + off + r];
+        if (del) {
+          F2 wv{qv[0], 0.f};
+#pragma unroll
+          for (int jj = 0; jj < BM - 1; ++jj) {
+            if (jj < m - 1) {
+              const float u = qv[jj + 1];
+              const F2 k1{cfr[4 * jj], cfr[4 * jj + 1]}, k2{cfr[4 * jj + 2], cfr[4 * jj + 3]};
+              F2 out, wn;
+              if (__double_as_longlong(st.rot[4 * jj + 2]) != 0) {
+                out = aa::df_axpy_f(wv, k1, u);
+                wn = aa::df_axpy_ff(u, k2, wv);
+              } else {
+                out = aa::df_axpy_ff(u, k1, wv);
+                wn = aa::df_axpy_f(wv, k2, u);
+              }
+              wv = wn;
+              qv[jj] = out.h;
+              a.Q[(int64_t)jj * a.N + off + r] = out.h;
+            }
+          }
+        }
+        // Q'^T f (rhs), Q'^T df (R column), Q'^T q'_{k-1} (delayed T row)
+#pragma unroll
+        for (int jj = 0; jj < BM; ++jj)
+          if (jj < k) {
+            aa::prod_f(f2, qv[jj], p, q);
+            aa::acc_add(aS[3 + jj], aC[3 + jj], p, q);
+            aa::prod_f(d2, qv[jj], p, q);
+            aa::acc_add(aS[3 + BM + jj], aC[3 + BM + jj], p, q);
+            if (jj + 1 < k) {
+              p = __fmul_rn(qv[jj], qv[k - 1]);
+              q = __fmaf_rn(qv[jj], qv[k - 1], -p);
+              aa::acc_add(aS[3 + 2 * BM + jj], aC[3 + 2 * BM + jj], p, q);
+            }
+          }
+      }
+      (void)nd;
+      {
+        double vals[BNDOT];
+#pragma unroll
+        for (int d = 0; d < BNDOT; ++d) vals[d] = aa::f2d(aS[d]) + aa::f2d(aC[d]);
+        block_reduce<NT>(vals, BNDOT, wbuf, st);
+      }
+      // ---- warp 0: stop test, R column, T row, projection coefficients
+      if (warp == 0) {
+        const double fn2 = st.red[0];
+        const double resid = sqrt(fn2) / (st.scale > 0 ? st.scale : 1.0);
+        if (lane == 0) {
+          if (it == 0 && a.warm && !st.fallback && !(resid < 1.0)) {
+            // the warm start is worse than x_0 = 0: restart from zero
+            st.fallback = 1;
+          } else if (!isfinite(fn2)) {
+            st.done = 1;
+            st.status = AA_ENONFINITE;
+          } else if (resid < a.tol || st.scale == 0.0) {
+            st.done = 1;
+            st.status = 0;
+          } else if (it >= a.max_iters) {
+            st.done = 1;
+            st.status = 1;
+          }
+          a.res[S.orig].iters = it;
+          a.res[S.orig].resid = resid;
+          a.res[S.orig].status = st.status;
+          a.res[S.orig].fallback = st.fallback ? 1 : 0;
+        }
+        __syncwarp();
+        if (!st.done && it > 0 && lane == 0) {
+          st.dfn2 = st.red[1];
+          if (del) {
+            for (int i = 0; i < BM * BM; ++i) {
+              const int jj = i / BM, ll = i % BM;
+              st.R[i] = (jj < k && ll < k) ? st.Rn[i] : 0.0;
+              st.T[i] = st.Tn[i];
+            }
+            for (int jj = 0; jj < k; ++jj) st.sig[jj] = st.rot[4 * jj + 3];
+            st.pend = 0;
+          }
+          for (int jj = 0; jj < k; ++jj) st.rhs[jj] = st.sig[jj] * st.red[3 + jj];
+          st.vscale = st.dfn2 > 0.0 ? 1.0 / sqrt(st.dfn2) : 1.0;
+          if (k > 0) {
+            for (int l = 0; l + 1 < k; ++l)
+              st.T[(k - 1) * BM + l] = st.sig[l] * st.sig[k - 1] * st.red[3 + 2 * BM + l];
+            for (int l = k - 1; l < BM; ++l) st.T[(k - 1) * BM + l] = (l == k - 1) ? 1.0 : 0.0;
+            for (int jj = 0; jj < k; ++jj) {
+              double v = st.sig[jj] * st.red[3 + BM + jj];
+              for (int l = 0; l < jj; ++l) v -= st.T[jj * BM + l] * st.rcol[l];
+              st.rcol[jj] = v;
+            }
+            for (int jj = 0; jj < k; ++jj) st.coef[jj] = st.sig[jj] * st.rcol[jj];
+          }
+        }
+        __syncwarp();
+        if (!st.done && it > 0 && k == 0)
+          finalize_b(st, m, 0, sqrt(st.red[1]), st.red[2], 1.0, head_new, a.breakdown_tol, lane);
+      }
+      __syncthreads();
+      if (st.done) break;
+      if (it == 0 && st.fallback == 1) {
+        for (int64_t r = tid; r < n; r += NT) Xc[r] = 0.0;
+        if (tid == 0) st.fallback = 2;
+        __syncthreads();
+        it = -1;
+        continue;
+      }
+      if (it > 0 && k > 0) {
+        // ---- projection pass: v = Delta f - Q r, new column, ||v||, v.f
+        for (int jj = tid; jj < k; jj += NT) {
+          const F2 cc = aa::d2f2(-st.coef[jj]);
+          cfc[2 * jj] = cc.h;
+          cfc[2 * jj + 1] = cc.l;
+        }
+        if (tid == 0) {
+          const F2 vs = aa::d2f2(st.vscale);
+          cfv[0] = vs.h;
+          cfv[1] = vs.l;
+        }
+        __syncthreads();
+        float vS[2] = {0.f, 0.f}, vC[2] = {0.f, 0.f};
+        for (int64_t r = tid; r < n; r += NT) {
+          F2 acc = aa::d2f2(DF[r]);
+#pragma unroll
+          for (int jj = 0; jj < BM; ++jj)
+            if (jj < k) acc = aa::df_axpy_f(acc, F2{cfc[2 * jj], cfc[2 * jj + 1]},
+                                            a.Q[(int64_t)jj * a.N + off + r]);
+          float p, q;
+          aa::prod_ff(acc, F2{cfv[0], cfv[1]}, p, q);
+          a.Q[(int64_t)k * a.N + off + r] = __fadd_rn(p, q);
+          aa::prod_ff(acc, acc, p, q);
+          aa::acc_add(vS[0], vC[0], p, q);
+          aa::prod_ff(acc, aa::d2f2(FP[r]), p, q);
+          aa::acc_add(vS[1], vC[1], p, q);
+        }
+        double vals[2] = {aa::f2d(vS[0]) + aa::f2d(vC[0]), aa::f2d(vS[1]) + aa::f2d(vC[1])};
+        block_reduce<NT>(vals, 2, wbuf, st);
+        if (warp == 0)
+          finalize_b(st, m, k, sqrt(st.red[0]), st.red[1], st.vscale, head_new, a.breakdown_tol,
+                     lane);
+        __syncthreads();
+      }
+      // ---- update pass: x_{i+1} = G(x_i) - dG gamma
+      const int ng = (it == 0) ? 0 : st.c;
+      for (int jj = tid; jj < BM; jj += NT) {
+        const F2 gg = aa::d2f2(-st.gphys[jj]);
+        cfg[2 * jj] = gg.h;
+        cfg[2 * jj + 1] = gg.l;
+      }
+      if (tid == 0) {
+        unsigned mk = 0;
+        for (int jj = 0; jj < m; ++jj)
+          if (st.gphys[jj] != 0.0) mk |= 1u << jj;
+        st.gmask = mk;
+      }
+      __syncthreads();
+      const unsigned gmask = st.gmask;
+      for (int64_t r = tid; r < n; r += NT) {
+        if (ng == 0) {
+          Xn[r] = GP[r];
+          continue;
+        }
+        F2 acc = aa::d2f2(GP[r]);
+#pragma unroll
+        for (int jj = 0; jj < BM; ++jj)
+          if ((gmask >> jj) & 1u)
+            acc = aa::df_axpy_f(acc, F2{cfg[2 * jj], cfg[2 * jj + 1]},
+                                a.DG[(int64_t)jj * a.N + off + r]);
+        Xn[r] = aa::f22d(acc);
+      }
+      __syncthreads();
+      double *tmp = Xc;
+      Xc = Xn;
+      Xn = tmp;
+    }
+    // leave the returned iterate in X0
+    if (Xc != a.X0 + off)
+      for (int64_t r = tid; r < n; r += NT) a.X0[off + r] = Xc[r];
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+struct aa_batch {
+  int count, m;
+  int64_t N;
+  std::vector<Solve> hsolves;
+  std::vector<int64_t> side;
+  Solve *dsolves;
+  Result *dres;
+  double *X0, *X1, *GP, *FP, *DF, *src, *Xinit;
+  float *Q, *DG;
+  unsigned *queue;
+  double tol, bd_tol;
+  int max_iters, block, ctas_per_sm;
+  cudaGraphExec_t gexec;
+  cudaGraph_t graph;
+  cudaStream_t gstream;
+};
+
+static int64_t round_up64(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
+
+extern "C" int aa_batch_create(const aa_batch_desc *d, aa_batch **out) {
+  if (!d || !out || d->count < 1 || !d->side || !d->lambda) return AA_EINVAL;
+  if (d->m < 1 || d->m > BM) return AA_EINVAL;
+  *out = nullptr;
+  aa_batch *b = new (std::nothrow) aa_batch();
+  if (!b) return AA_ENOMEM;
+  b->count = d->count;
+  b->m = d->m;
+  b->tol = d->tol > 0 ? d->tol : 1e-8;
+  b->bd_tol = 1e-14;
+  b->max_iters = d->max_iters > 0 ? d->max_iters : 100000;
+  b->block = d->block;
+  b->ctas_per_sm = d->ctas_per_sm;
+  // largest solves first
+  std::vector<int> order(d->count);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int x, int y) { return d->side[x] > d->side[y]; });
+  int64_t off = 0;
+  b->hsolves.resize(d->count);
+  for (int i = 0; i < d->count; ++i) {
+    const int o = order[i];
+    if (d->side[o] < 1 || d->side[o] > 46340) {
+      delete b;
+      return AA_EINVAL;
+    }
+    Solve S;
+    S.off = off;
+    S.s = (int32_t)d->side[o];
+    S.orig = o;
+    S.lambda = d->lambda[o];
+    S.scale = 0.0;
+    b->hsolves[i] = S;
+    off += round_up64((int64_t)S.s * S.s, 64);
+  }
+  b->N = off;
+  const size_t nd = (size_t)b->N * sizeof(double), nf = (size_t)b->N * sizeof(float);
+  bool ok = cudaMalloc(&b->X0, nd) == cudaSuccess && cudaMalloc(&b->X1, nd) == cudaSuccess &&
+            cudaMalloc(&b->GP, nd) == cudaSuccess && cudaMalloc(&b->FP, nd) == cudaSuccess &&
+            cudaMalloc(&b->DF, nd) == cudaSuccess &&
+            cudaMalloc(&b->Q, nf * b->m) == cudaSuccess &&
+            cudaMalloc(&b->DG, nf * b->m) == cudaSuccess &&
+            cudaMalloc(&b->dsolves, sizeof(Solve) * b->count) == cudaSuccess &&
+            cudaMalloc(&b->dres, sizeof(Result) * b->count) == cudaSuccess &&
+            cudaMalloc(&b->queue, sizeof(unsigned)) == cudaSuccess;
+  // stopping scale ||G(0)||: at u = 0 every neighbour is 0 and e^0 = 1, so
+  // G(0)_p = h^2 (lambda + src_p) / 4.
+  {
+    std::vector<int64_t> corig(d->count);
+    int64_t so = 0;
+    for (int i = 0; i < d->count; ++i) {
+      corig[i] = so;
+      so += d->side[i] * d->side[i];
+    }
+    for (Solve &S : b->hsolves) {
+      const double h = 1.0 / (double)(S.s + 1);
+      const int64_t n = (int64_t)S.s * S.s;
+      double acc = 0.0;
+      for (int64_t p = 0; p < n; ++p) {
+        const double v = S.lambda + (d->src_host ? d->src_host[corig[S.orig] + p] : 0.0);
+        acc += v * v;
+      }
+      S.scale = h * h / 4.0 * sqrt(acc);
+    }
+  }
+  if (ok && d->src_host) {
+    ok = cudaMalloc(&b->src, nd) == cudaSuccess;
+    if (ok) {
+      std::vector<double> hs(b->N, 0.0);
+      int64_t so = 0;  // src_host is in the caller's order, concatenated
+      std::vector<int64_t> corig(d->count);
+      for (int i = 0; i < d->count; ++i) {
+        corig[i] = so;
+        so += d->side[i] * d->side[i];
+      }
+      for (const Solve &S : b->hsolves)
+        memcpy(&hs[S.off], d->src_host + corig[S.orig], sizeof(double) * (size_t)S.s * S.s);
+      ok = cudaMemcpy(b->src, hs.data(), nd, cudaMemcpyHostToDevice) == cudaSuccess;
+    }
+  }
+  if (ok)
+    ok = cudaMemcpy(b->dsolves, b->hsolves.data(), sizeof(Solve) * b->count,
+                    cudaMemcpyHostToDevice) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    aa_batch_destroy(b);
+    return AA_ENOMEM;
+  }
+  *out = b;
+  return AA_OK;
+}
+
+extern "C" void aa_batch_destroy(aa_batch *b) {
+  if (!b) return;
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  cudaFree(b->X0);
+  cudaFree(b->X1);
+  cudaFree(b->GP);
+  cudaFree(b->FP);
+  cudaFree(b->DF);
+  cudaFree(b->Q);
+  cudaFree(b->DG);
+  cudaFree(b->src);
+  cudaFree(b->Xinit);
+  cudaFree(b->dsolves);
+  cudaFree(b->dres);
+  cudaFree(b->queue);
+  delete b;
+}
+
+template <int NT>
+static cudaError_t launch_batch(const BArgs &a, int grid, cudaStream_t s) {
+  batch_kernel<NT><<<grid, NT, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+static cudaError_t enqueue(aa_batch *b, int block, int cps, cudaStream_t s) {
+  int dev = 0, nsm = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  BArgs a;
+  a.solves = b->dsolves;
+  a.res = b->dres;
+  a.count = b->count;
+  a.m = b->m;
+  a.max_iters = b->max_iters;
+  a.tol = b->tol;
+  a.breakdown_tol = b->bd_tol;
+  a.X0 = b->X0;
+  a.X1 = b->X1;
+  a.GP = b->GP;
+  a.FP = b->FP;
+  a.DF = b->DF;
+  a.Q = b->Q;
+  a.DG = b->DG;
+  a.N = b->N;
+  a.src = b->src;
+  a.warm = b->Xinit != nullptr;
+  a.queue = b->queue;
+  cudaError_t e = cudaMemsetAsync(b->queue, 0, sizeof(unsigned), s);
+  if (e == cudaSuccess)
+    e = b->Xinit ? cudaMemcpyAsync(b->X0, b->Xinit, (size_t)b->N * sizeof(double),
+                                   cudaMemcpyDeviceToDevice, s)
+                 : cudaMemsetAsync(b->X0, 0, (size_t)b->N * sizeof(double), s);
+  if (e != cudaSuccess) return e;
+  const int grid = nsm * (cps > 0 ? cps : 1);
+  switch (block) {
+    case 128: return launch_batch<128>(a, grid, s);
+    case 512: return launch_batch<512>(a, grid, s);
+    default: return launch_batch<256>(a, grid, s);
+  }
+}
+
+extern "C" int aa_batch_solve(aa_batch *b, int block, int ctas_per_sm, void *stream,
+                              double *ms_out) {
+  if (!b) return AA_EINVAL;
+  if (block != 128 && block != 256 && block != 512) block = 256;
+  if (ctas_per_sm < 1 || ctas_per_sm > 4) ctas_per_sm = 1;
+  cudaStream_t s = (cudaStream_t)stream;
+  // The whole batch is one persistent kernel; it is captured once per
+  // (block, ctas_per_sm) into a CUDA graph and replayed.
+  if (!b->gexec || b->block != block || b->ctas_per_sm != ctas_per_sm) {
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->gexec = nullptr;
+    b->graph = nullptr;
+    cudaStream_t cs;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return AA_ECUDA;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t e2 = enqueue(b, block, ctas_per_sm, cs);
+      e = cudaStreamEndCapture(cs, &b->graph);
+      if (e2 != cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->gexec, b->graph, 0);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return AA_ECUDA;
+    }
+    b->block = block;
+    b->ctas_per_sm = ctas_per_sm;
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, s);
+  cudaError_t e = cudaGraphLaunch(b->gexec, s);
+  cudaEventRecord(e1, s);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (ms_out) *ms_out = ms;
+  return e == cudaSuccess ? AA_OK : AA_ECUDA;
+}
+
+extern "C" int aa_batch_results(aa_batch *b, int32_t *iters, double *resid, int32_t *status) {
+  if (!b) return AA_EINVAL;
+  std::vector<Result> r(b->count);
+  if (cudaMemcpy(r.data(), b->dres, sizeof(Result) * b->count, cudaMemcpyDeviceToHost) !=
+      cudaSuccess)
+    return AA_ECUDA;
+  for (int i = 0; i < b->count; ++i) {
+    if (iters) iters[i] = r[i].iters;
+    if (resid) resid[i] = r[i].resid;
+    if (status) status[i] = r[i].status;
+  }
+  return AA_OK;
+}
+
+extern "C" int aa_batch_solution(aa_batch *b, int idx, double *x_host) {
+  if (!b || idx < 0 || idx >= b->count || !x_host) return AA_EINVAL;
+  for (const Solve &S : b->hsolves)
+    if (S.orig == idx) {
+      if (cudaMemcpy(x_host, b->X0 + S.off, sizeof(double) * (size_t)S.s * S.s,
+                     cudaMemcpyDeviceToHost) != cudaSuccess)
+        return AA_ECUDA;
+      return AA_OK;
+    }
+  return AA_EINVAL;
+}
+
+extern "C" int64_t aa_batch_rows(const aa_batch *b) { return b ? b->N : 0; }
+
+extern "C" int aa_batch_set_x0(aa_batch *b, const double *x0_host) {
+  if (!b) return AA_EINVAL;
+  if (!x0_host) {  // back to x_0 = 0
+    cudaFree(b->Xinit);
+    b->Xinit = nullptr;
+  } else {
+    if (!b->Xinit && cudaMalloc(&b->Xinit, (size_t)b->N * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      return AA_ENOMEM;
+    }
+    std::vector<double> hx(b->N, 0.0);
+    std::vector<int64_t> corig(b->count);
+    int64_t so = 0;
+    std::vector<int64_t> side_orig(b->count);
+    for (const Solve &S : b->hsolves) side_orig[S.orig] = S.s;
+    for (int i = 0; i < b->count; ++i) {
+      corig[i] = so;
+      so += side_orig[i] * side_orig[i];
+    }
+    for (const Solve &S : b->hsolves)
+      memcpy(&hx[S.off], x0_host + corig[S.orig], sizeof(double) * (size_t)S.s * S.s);
+    if (cudaMemcpy(b->Xinit, hx.data(), (size_t)b->N * sizeof(double), cudaMemcpyHostToDevice) !=
+        cudaSuccess)
+      return AA_ECUDA;
+  }
+  // the captured graph embeds the x_0 copy: capture again on the next solve
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->gexec = nullptr;
+  b->graph = nullptr;
+  return AA_OK;
+}

@@ -88,6 +88,7 @@ struct PassArgs {
   uint8_t pslot[MMAX];             // K_UPDATE: dG physical slot of tile column qbase + i
   uint8_t dot_a[NDOT_MAX];         // dot d = sum_r tile[a][r] * tile[b][r]
   uint8_t dot_b[NDOT_MAX];
+  uint64_t dotcols[2];             // bit c: tile column c appears in a dot product
   // outputs (NULL when unused)
   void *out_q[MMAX];               // history slots written by the row program
   void *out_dg;                    // dG slot for Delta g (K_A step mode)

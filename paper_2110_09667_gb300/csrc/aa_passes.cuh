@@ -20,6 +20,7 @@
 #include <stdint.h>
 
 #include "aa_common.h"
+#include "aa_df.cuh"
 
 
 
@@ -33,16 +34,26 @@ constexpr int DEV_ETIMEOUT = -6;
 
 template <class QT> __device__ __forceinline__ double to_d(QT v);
 template <> __device__ __forceinline__ double to_d<double>(double v) { return v; }
-template <> __device__ __forceinline__ double to_d<float>(float v) { return (double)v; }
+// float/bf16 <-> double through integer operations (the hardware conversion
+// instructions run on the scarce FP64 pipe of this part).
+template <> __device__ __forceinline__ double to_d<float>(float v) { return f2d(v); }
 template <> __device__ __forceinline__ double to_d<__nv_bfloat16>(__nv_bfloat16 v) {
-  return (double)__bfloat162float(v);
+  return f2d(__bfloat162float(v));
 }
 template <class QT> __device__ __forceinline__ QT from_d(double v);
 template <> __device__ __forceinline__ double from_d<double>(double v) { return v; }
-template <> __device__ __forceinline__ float from_d<float>(double v) { return __double2float_rn(v); }
+template <> __device__ __forceinline__ float from_d<float>(double v) { return d2f_rn(v); }
 template <> __device__ __forceinline__ __nv_bfloat16 from_d<__nv_bfloat16>(double v) {
-  return __float2bfloat16_rn(__double2float_rn(v));
+  return __float2bfloat16_rn(d2f_rn(v));
 }
+template <class QT> __device__ __forceinline__ float q2f(QT v);
+template <> __device__ __forceinline__ float q2f<float>(float v) { return v; }
+template <> __device__ __forceinline__ float q2f<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <> __device__ __forceinline__ float q2f<double>(double v) { return (float)v; }  // unused
+template <class QT> __device__ __forceinline__ QT f2q(float v);
+template <> __device__ __forceinline__ float f2q<float>(float v) { return v; }
+template <> __device__ __forceinline__ __nv_bfloat16 f2q<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+template <> __device__ __forceinline__ double f2q<double>(float v) { return (double)v; }  // unused
 
 // ------------------------------------------------- mbarrier / bulk copies
 
@@ -104,6 +115,13 @@ struct Stage {
   __device__ __forceinline__ QT *q(int c) const {
     return (QT *)(base + (size_t)c * TR * 8);
   }
+  // an FP64 column after it was split in place into (hi, lo) floats
+  __device__ __forceinline__ float2 *p(int c) const { return (float2 *)(base + (size_t)c * TR * 8); }
+  __device__ __forceinline__ F2 f2(int c, int r) const {
+    const float2 v = p(c)[r];
+    return F2{v.x, v.y};
+  }
+  __device__ __forceinline__ void put(int c, int r, F2 v) const { p(c)[r] = make_float2(v.h, v.l); }
 };
 
 template <class QT>
@@ -156,6 +174,13 @@ constexpr int CO_COEF = 4 * MMAX + 1;  // coef[0..k)
 constexpr int CO_COEF2 = 5 * MMAX + 1; // coef2[0..k-1)
 constexpr int CO_MISC = 6 * MMAX + 1;  // rcself, vscale
 constexpr int CO_SIZE = 6 * MMAX + 4;
+// (hi, lo) float copies used by the FP32-pipe programs; projection and update
+// coefficients are stored negated.
+constexpr int CF_ROT = 0;               // per rotation: k1 (hi, lo), k2 (hi, lo)
+constexpr int CF_COEF = 4 * MMAX;       // -coef[j] (hi, lo)
+constexpr int CF_COEF2 = 6 * MMAX;      // -coef2[j] (hi, lo)
+constexpr int CF_MISC = 8 * MMAX;       // rcself (hi, lo), vscale (hi, lo)
+constexpr int CF_SIZE = 8 * MMAX + 4;
 
 template <class QT>
 __device__ __forceinline__ void row_program(const PassArgs &a, Stage st, int t, int r,
@@ -189,17 +214,27 @@ __device__ __forceinline__ void row_program(const PassArgs &a, Stage st, int t, 
       a.out_df[row] = df;
       if (a.k == 0) ((QT *)a.out_q[0])[row] = from_d<QT>(df);
       if (a.del) {
-        // QRDelete: sequential Givens rotations of adjacent columns; column
-        // j is final once rotation j has been applied.  Coefficients are
-        // folded with the stored columns' scales.
+        // QRDelete: sequential Givens rotations of adjacent columns, in the
+        // square-root-free scaled form (Gentleman 1973, Hammarling 1974):
+        // two multiply-adds per rotation, the scale factors folded into the
+        // column scales at the m x m level.  Column j is final once rotation
+        // j has been applied; w carries column j+1 (scale tracked on the
+        // device state).
         const int qb = a.qbase;
-        double carry = co[CO_ROT0] * to_d<QT>(st.q<QT>(qb)[r]);
+        double w = to_d<QT>(st.q<QT>(qb)[r]);
         for (int j = 0; j < a.m - 1; ++j) {
-          const double b = to_d<QT>(st.q<QT>(qb + j + 1)[r]);
+          const double u = to_d<QT>(st.q<QT>(qb + j + 1)[r]);
           const double *R = co + CO_ROT + 4 * j;
-          const double qj = R[0] * carry + R[1] * b;
-          carry = R[2] * carry + R[3] * b;
-          const QT qs = from_d<QT>(qj);
+          double out, wn;
+          if (__double_as_longlong(R[2]) != 0) {  // |c| >= |s| (integer test: no FP64 op)
+            out = fma(R[0], u, w);
+            wn = fma(R[1], w, u);
+          } else {
+            out = fma(R[0], w, u);
+            wn = fma(R[1], u, w);
+          }
+          w = wn;
+          const QT qs = from_d<QT>(out);
           ((QT *)a.out_q[j])[row] = qs;
           st.q<QT>(qb + j)[r] = qs;
         }
@@ -242,6 +277,128 @@ __device__ __forceinline__ void row_program(const PassArgs &a, Stage st, int t, 
       for (int i = 0; i < a.ng; ++i) xn -= co[CO_COEF + i] * to_d<QT>(st.q<QT>(a.qbase + i)[r]);
       a.out_x[row] = xn;
       if (a.stop_kind == 1) st.d(1)[r] = xn - st.d(1)[r];
+      break;
+    }
+    default:
+      break;
+  }
+}
+
+// Row programs with every n-space operation on the FP32/INT pipes, for
+// FP32/BF16 history storage.  FP64 inputs are split into (hi, lo) floats,
+// stored history entries are floats (exact), the residual differences stay
+// FP64 (3 adds per row).  Columns that feed the dot phase are left in shared
+// memory as (hi, lo) pairs.
+template <class QT>
+__device__ __forceinline__ void row_program_df(const PassArgs &a, Stage st, int t, int r,
+                                               const double *co, const float *cf) {
+  const int64_t row = (int64_t)t * TR + r;
+  switch (a.kind) {
+    case K_INIT: {
+      const double x = st.d(0)[r], g = st.d(1)[r];
+      const double f = g - x;
+      a.out_f[row] = f;
+      a.out_g[row] = g;
+      a.out_x[row] = g;
+      st.put(0, r, d2f2(f));
+      break;
+    }
+    case K_A: {
+      double df;
+      if (a.step_mode) {
+        const double x = st.d(0)[r], g = st.d(1)[r], gp = st.d(2)[r], fp = st.d(3)[r];
+        const double f = g - x;
+        df = f - fp;
+        const double dg = g - gp;
+        ((QT *)a.out_dg)[row] = from_d<QT>(dg);
+        a.out_f[row] = f;
+        a.out_g[row] = g;
+        st.put(0, r, d2f2(f));
+        st.put(1, r, d2f2(df));
+      } else {
+        df = st.d(0)[r];
+        st.put(0, r, d2f2(df));
+      }
+      a.out_df[row] = df;
+      if (a.k == 0) ((QT *)a.out_q[0])[row] = from_d<QT>(df);
+      if (a.del) {
+        // QRDelete rotation (scaled form, see row_program) in (hi, lo) floats.
+        const int qb = a.qbase;
+        F2 w{q2f<QT>(st.q<QT>(qb)[r]), 0.f};
+        for (int j = 0; j < a.m - 1; ++j) {
+          const float u = q2f<QT>(st.q<QT>(qb + j + 1)[r]);
+          const float *R = cf + CF_ROT + 4 * j;
+          const F2 k1{R[0], R[1]}, k2{R[2], R[3]};
+          F2 out, wn;
+          if (__double_as_longlong(co[CO_ROT + 4 * j + 2]) != 0) {
+            out = df_axpy_f(w, k1, u);
+            wn = df_axpy_ff(u, k2, w);
+          } else {
+            out = df_axpy_ff(u, k1, w);
+            wn = df_axpy_f(w, k2, u);
+          }
+          w = wn;
+          const QT qs = f2q<QT>(out.h);
+          ((QT *)a.out_q[j])[row] = qs;
+          st.q<QT>(qb + j)[r] = qs;
+        }
+      }
+      break;
+    }
+    case K_PROJ: {
+      const int qb = a.qbase;
+      F2 acc = d2f2(st.d(0)[r]);
+      if (a.orth == O_DCGS2 && (a.flags & 0x100u)) {
+        const int kk = a.k - 1;
+        float p, e;
+        prod_f(F2{cf[CF_MISC], cf[CF_MISC + 1]}, q2f<QT>(st.q<QT>(qb + kk)[r]), p, e);
+        F2 qn = fast_two_sum(p, e);
+        for (int j = 0; j < kk; ++j)
+          qn = df_axpy_f(qn, F2{cf[CF_COEF2 + 2 * j], cf[CF_COEF2 + 2 * j + 1]},
+                         q2f<QT>(st.q<QT>(qb + j)[r]));
+        const QT qs = f2q<QT>(qn.h);
+        ((QT *)a.out_q[kk])[row] = qs;
+        st.q<QT>(qb + kk)[r] = qs;
+      }
+      for (int j = a.j0; j < a.k; ++j)
+        acc = df_axpy_f(acc, F2{cf[CF_COEF + 2 * j], cf[CF_COEF + 2 * j + 1]},
+                        q2f<QT>(st.q<QT>(qb + j - a.j0)[r]));
+      float p, e;
+      prod_ff(acc, F2{cf[CF_MISC + 2], cf[CF_MISC + 3]}, p, e);
+      ((QT *)a.out_q[a.k])[row] = f2q<QT>(__fadd_rn(p, e));
+      st.put(0, r, acc);
+      if (a.step_mode) st.put(1, r, d2f2(st.d(1)[r]));  // f feeds v.f (and q_{k-1}.f)
+      break;
+    }
+    case K_CGS2B: {
+      F2 acc = d2f2(st.d(0)[r]);
+      for (int j = 0; j < a.k; ++j)
+        acc = df_axpy_f(acc, F2{cf[CF_COEF + 2 * j], cf[CF_COEF + 2 * j + 1]},
+                        q2f<QT>(st.q<QT>(a.qbase + j)[r]));
+      a.out_df[row] = f22d(acc);
+      st.put(0, r, acc);
+      break;
+    }
+    case K_MGS: {
+      F2 acc = d2f2(st.d(0)[r]);
+      acc = df_axpy_f(acc, F2{cf[CF_COEF + 2 * (a.jm - 1)], cf[CF_COEF + 2 * (a.jm - 1) + 1]},
+                      q2f<QT>(st.q<QT>(a.qbase)[r]));
+      a.out_df[row] = f22d(acc);
+      st.put(0, r, acc);
+      break;
+    }
+    case K_UPDATE: {
+      F2 acc = d2f2(st.d(0)[r]);
+      for (int i = 0; i < a.ng; ++i)
+        acc = df_axpy_f(acc, F2{cf[CF_COEF + 2 * i], cf[CF_COEF + 2 * i + 1]},
+                        q2f<QT>(st.q<QT>(a.qbase + i)[r]));
+      const double xn = f22d(acc);
+      a.out_x[row] = xn;
+      if (a.stop_kind == 1) st.put(1, r, d2f2(xn - st.d(1)[r]));
+      break;
+    }
+    case K_LSQ: {
+      st.put(0, r, d2f2(st.d(0)[r]));
       break;
     }
     default:
@@ -362,6 +519,7 @@ static __device__ void prepare_delete(const PassArgs &a, DevState *S, const Epi 
     }
     __syncwarp();
   }
+  double tau = e.sig[0];  // scale of the carried column (lane 0 only)
   for (int j = 0; j + 1 < M; ++j) {
     const double av = e.r(j, j), bv = e.r(j + 1, j);
     const double rho = hypot(av, bv);
@@ -379,10 +537,28 @@ static __device__ void prepare_delete(const PassArgs &a, DevState *S, const Epi 
     __syncwarp();
     if (lane == 0) {
       e.r(j + 1, j) = 0.0;
-      S->rot[4 * j + 0] = c;
-      S->rot[4 * j + 1] = s * e.sig[j + 1];
-      S->rot[4 * j + 2] = -s;
-      S->rot[4 * j + 3] = c * e.sig[j + 1];
+      // scaled rotation of (carry, column j+1): carry has scale tau, the
+      // stored column j+1 has scale sig_{j+1}; pick the form whose
+      // multipliers stay bounded.
+      const double sj1 = e.sig[j + 1];
+      double k1, k2, sout, type;
+      if (fabs(c) >= fabs(s)) {
+        k1 = s * sj1 / (c * tau);
+        k2 = -s * tau / (c * sj1);
+        sout = c * tau;
+        tau = c * sj1;
+        type = 1.0;
+      } else {
+        k1 = c * tau / (s * sj1);
+        k2 = -c * sj1 / (s * tau);
+        sout = s * sj1;
+        tau = -s * tau;
+        type = 0.0;
+      }
+      S->rot[4 * j + 0] = k1;
+      S->rot[4 * j + 1] = k2;
+      S->rot[4 * j + 2] = type;
+      S->rot[4 * j + 3] = sout;
     }
     if (icwy_rot) {
       for (int i = lane; i < M; i += 32) {  // columns j, j+1
@@ -516,7 +692,7 @@ static __device__ void epilogue(const PassArgs &a, double *scratch, int lane) {
       vec_in(e.sig, S->sig, m, lane);
       vec_in(e.rcol, S->rcol, m, lane);
       if (a.del) {
-        for (int j = lane; j < k; j += 32) e.sig[j] = 1.0;
+        for (int j = lane; j < k; j += 32) e.sig[j] = S->rot[4 * j + 3];
         if (lane == 0) S->pend_del = 0;
         __syncwarp();
       }
@@ -657,12 +833,21 @@ static __device__ void epilogue(const PassArgs &a, double *scratch, int lane) {
 }
 
 // ---------------------------------------------------------------- kernel
+//
+// MODE 0: FP64 storage, FP64 arithmetic throughout (exact FP64 path).
+// MODE 1: FP64 storage and FP64 row programs; dot products on the FP32
+//         pipe from (hi, lo) splits, accumulated per lane in compensated
+//         float pairs and folded into FP64 once per tile.
+// MODE 2: FP32/BF16 storage; row programs and dot products on the FP32/INT
+//         pipes (row_program_df), partial sums folded into FP64 every
+//         second tile.
 
-template <class QT, int DPW>
+template <class QT, int DPW, int MODE = 0>
 __global__ void __launch_bounds__(NT) pass_kernel(const __grid_constant__ PassArgs a, int nstages) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t bars[STAGES];
   __shared__ double co[CO_SIZE];
+  __shared__ float cf[MODE == 2 ? CF_SIZE : 1];
   __shared__ uint8_t sda[NDOT_MAX], sdb[NDOT_MAX];
   __shared__ int s_last;
   __shared__ int s_err;
@@ -700,6 +885,32 @@ __global__ void __launch_bounds__(NT) pass_kernel(const __grid_constant__ PassAr
     fence_mbar_init();
   }
   __syncthreads();
+  if constexpr (MODE == 2) {
+    // (hi, lo) float copies of the coefficients; projection/update
+    // coefficients negated.
+    for (int j = tid; j < MMAX; j += NT) {
+      if (j < a.m - 1) {
+        const F2 k1 = d2f2(co[CO_ROT + 4 * j]), k2 = d2f2(co[CO_ROT + 4 * j + 1]);
+        cf[CF_ROT + 4 * j] = k1.h;
+        cf[CF_ROT + 4 * j + 1] = k1.l;
+        cf[CF_ROT + 4 * j + 2] = k2.h;
+        cf[CF_ROT + 4 * j + 3] = k2.l;
+      }
+      const F2 c1 = d2f2(-co[CO_COEF + j]), c2 = d2f2(-co[CO_COEF2 + j]);
+      cf[CF_COEF + 2 * j] = c1.h;
+      cf[CF_COEF + 2 * j + 1] = c1.l;
+      cf[CF_COEF2 + 2 * j] = c2.h;
+      cf[CF_COEF2 + 2 * j + 1] = c2.l;
+    }
+    if (tid == 0) {
+      const F2 rc = d2f2(co[CO_MISC]), vs = d2f2(co[CO_MISC + 1]);
+      cf[CF_MISC] = rc.h;
+      cf[CF_MISC + 1] = rc.l;
+      cf[CF_MISC + 2] = vs.h;
+      cf[CF_MISC + 3] = vs.l;
+    }
+    __syncthreads();
+  }
 
   if (tid == 0) {
     for (int s = 0; s < nstages; ++s) {
@@ -709,8 +920,14 @@ __global__ void __launch_bounds__(NT) pass_kernel(const __grid_constant__ PassAr
   }
 
   double acc[DPW];
+  float accS[MODE ? DPW : 1], accC[MODE ? DPW : 1];
 #pragma unroll
   for (int i = 0; i < DPW; ++i) acc[i] = 0.0;
+  if constexpr (MODE != 0) {
+#pragma unroll
+    for (int i = 0; i < DPW; ++i) accS[i] = accC[i] = 0.f;
+  }
+  constexpr int FLUSH = (MODE == 2) ? 2 : 1;  // tiles per fold into FP64
 
   int it = 0;
   for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++it) {
@@ -723,7 +940,18 @@ __global__ void __launch_bounds__(NT) pass_kernel(const __grid_constant__ PassAr
     __syncthreads();
     if (s_err) break;
     if (tid >= rt && tid < rows) load_tail_row<QT>(a, st, t, tid);
-    if (tid < rows) row_program<QT>(a, st, t, tid, co);
+    if (tid < rows) {
+      if constexpr (MODE == 2) {
+        row_program_df<QT>(a, st, t, tid, co, cf);
+      } else {
+        row_program<QT>(a, st, t, tid, co);
+        if constexpr (MODE == 1) {
+          // the columns that feed the dot phase, as (hi, lo) floats
+          for (int c = 0; c < a.ncol; ++c)
+            if ((a.dotcols[c >> 6] >> (c & 63)) & 1ull) st.put(c, tid, d2f2(st.d(c)[tid]));
+        }
+      }
+    }
     __syncthreads();
     // dot phase: warp w owns dots w, w + NWARP, ...
 #pragma unroll
@@ -731,10 +959,49 @@ __global__ void __launch_bounds__(NT) pass_kernel(const __grid_constant__ PassAr
       const int d = warp + NWARP * i;
       if (d < a.ndots) {
         const int ca = sda[d], cb = sdb[d];
-        const bool qa = ca >= a.qbase, qb = cb >= a.qbase;
-        double sum = 0.0;
-        for (int r = lane; r < rows; r += 32) sum += ldv<QT>(st, ca, r, qa) * ldv<QT>(st, cb, r, qb);
-        acc[i] += sum;
+        if constexpr (MODE == 0) {
+          const bool qa = ca >= a.qbase, qb = cb >= a.qbase;
+          double sum = acc[i];
+          for (int r = lane; r < rows; r += 32)
+            sum = fma(ldv<QT>(st, ca, r, qa), ldv<QT>(st, cb, r, qb), sum);
+          acc[i] = sum;
+        } else {
+          const bool qa = (MODE == 2) && ca >= a.qbase, qb = (MODE == 2) && cb >= a.qbase;
+          float S = accS[i], C = accC[i], p, e;
+          if (qa && qb) {
+            for (int r = lane; r < rows; r += 32) {
+              const float x = q2f<QT>(st.q<QT>(ca)[r]), y = q2f<QT>(st.q<QT>(cb)[r]);
+              p = __fmul_rn(x, y);
+              e = __fmaf_rn(x, y, -p);
+              acc_add(S, C, p, e);
+            }
+          } else if (qa || qb) {
+            const int cq = qa ? ca : cb, cv = qa ? cb : ca;
+            for (int r = lane; r < rows; r += 32) {
+              prod_f(st.f2(cv, r), q2f<QT>(st.q<QT>(cq)[r]), p, e);
+              acc_add(S, C, p, e);
+            }
+          } else {
+            for (int r = lane; r < rows; r += 32) {
+              prod_ff(st.f2(ca, r), st.f2(cb, r), p, e);
+              acc_add(S, C, p, e);
+            }
+          }
+          accS[i] = S;
+          accC[i] = C;
+        }
+      }
+    }
+    if constexpr (MODE != 0) {
+      if ((it + 1) % FLUSH == 0) {
+#pragma unroll
+        for (int i = 0; i < DPW; ++i) {
+          if (warp + NWARP * i < a.ndots) {
+            acc[i] += f2d(accS[i]);
+            acc[i] += f2d(accC[i]);
+            accS[i] = accC[i] = 0.f;
+          }
+        }
       }
     }
     __syncthreads();
@@ -743,6 +1010,15 @@ __global__ void __launch_bounds__(NT) pass_kernel(const __grid_constant__ PassAr
       if (tn < a.ntiles) {
         fence_proxy_async();
         issue_tile<QT>(a, st, tn, &bars[s]);
+      }
+    }
+  }
+  if constexpr (MODE != 0) {
+#pragma unroll
+    for (int i = 0; i < DPW; ++i) {
+      if (warp + NWARP * i < a.ndots) {
+        acc[i] += f2d(accS[i]);
+        acc[i] += f2d(accC[i]);
       }
     }
   }
@@ -777,11 +1053,14 @@ __global__ void __launch_bounds__(NT) pass_kernel(const __grid_constant__ PassAr
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  // Last CTA: finish the reduction in CTA order (bit-reproducible).
-  for (int d = tid; d < a.ndots; d += NT) {
+  // Last CTA: finish the reduction.  Warp w owns dots w, w + NWARP, ...;
+  // lane l sums the partials of CTAs l, l + 32, ... and a fixed butterfly
+  // combines the lanes (bit-reproducible).
+  for (int d = warp; d < a.ndots; d += NWARP) {
     double v = 0.0;
-    for (int b = 0; b < (int)gridDim.x; ++b) v += __ldcg(&a.partials[(size_t)b * NDOT_MAX + d]);
-    S->red[d] = v;
+    for (int b = lane; b < (int)gridDim.x; b += 32) v += __ldcg(&a.partials[(size_t)b * NDOT_MAX + d]);
+    v = warp_sum(v);
+    if (lane == 0) S->red[d] = v;
   }
   __threadfence();
   __syncthreads();
@@ -794,11 +1073,11 @@ __global__ void __launch_bounds__(NT) pass_kernel(const __grid_constant__ PassAr
 
 // ------------------------------------------------------------ host launch
 
-template <class QT, int DPW>
+template <class QT, int DPW, int MODE>
 static cudaError_t launch_t(const PassArgs &a, int grid, size_t smem, int nstages,
                             cudaStream_t stream) {
   static bool attr_set = false;  // per instantiation
-  auto kern = pass_kernel<QT, DPW>;
+  auto kern = pass_kernel<QT, DPW, MODE>;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          227 * 1024 - 8 * 1024);
@@ -809,17 +1088,17 @@ static cudaError_t launch_t(const PassArgs &a, int grid, size_t smem, int nstage
   return cudaGetLastError();
 }
 
-template <class QT, int DPW>
+template <class QT, int DPW, int MODE>
 static int occupancy_t(size_t smem) {
   int nb = 0;
-  auto kern = pass_kernel<QT, DPW>;
+  auto kern = pass_kernel<QT, DPW, MODE>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024 - 8 * 1024);
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, NT, smem) != cudaSuccess) return 1;
   return nb < 1 ? 1 : nb;
 }
 
-template <class QT>
-static inline cudaError_t launch_q(const PassArgs &a, int nsm, int *grid_out, cudaStream_t stream) {
+template <class QT, int MODE>
+static inline cudaError_t launch_qm(const PassArgs &a, int nsm, int *grid_out, cudaStream_t stream) {
   const size_t stage = (size_t)a.ncol * TR * 8;
   const size_t budget = 227 * 1024 - 8 * 1024;
   int nstages = (stage * STAGES <= budget) ? STAGES : 1;
@@ -829,18 +1108,18 @@ static inline cudaError_t launch_q(const PassArgs &a, int nsm, int *grid_out, cu
   if (smem > budget) return cudaErrorInvalidConfiguration;
   int occ;
   const int dpw_need = (a.ndots + NWARP - 1) / NWARP;
-  if (dpw_need <= 1) occ = occupancy_t<QT, 1>(smem);
-  else if (dpw_need <= 4) occ = occupancy_t<QT, 4>(smem);
-  else if (dpw_need <= 16) occ = occupancy_t<QT, 16>(smem);
-  else occ = occupancy_t<QT, 32>(smem);
+  if (dpw_need <= 1) occ = occupancy_t<QT, 1, MODE>(smem);
+  else if (dpw_need <= 4) occ = occupancy_t<QT, 4, MODE>(smem);
+  else if (dpw_need <= 16) occ = occupancy_t<QT, 16, MODE>(smem);
+  else occ = occupancy_t<QT, 32, MODE>(smem);
   int grid = nsm * occ;
   if (grid > a.ntiles) grid = a.ntiles;
   if (grid < 1) grid = 1;
   *grid_out = grid;
-  if (dpw_need <= 1) return launch_t<QT, 1>(a, grid, smem, nstages, stream);
-  if (dpw_need <= 4) return launch_t<QT, 4>(a, grid, smem, nstages, stream);
-  if (dpw_need <= 16) return launch_t<QT, 16>(a, grid, smem, nstages, stream);
-  return launch_t<QT, 32>(a, grid, smem, nstages, stream);
+  if (dpw_need <= 1) return launch_t<QT, 1, MODE>(a, grid, smem, nstages, stream);
+  if (dpw_need <= 4) return launch_t<QT, 4, MODE>(a, grid, smem, nstages, stream);
+  if (dpw_need <= 16) return launch_t<QT, 16, MODE>(a, grid, smem, nstages, stream);
+  return launch_t<QT, 32, MODE>(a, grid, smem, nstages, stream);
 }
 
 }  // namespace aa

@@ -1,10 +1,10 @@
 // aa_passes_f32.cu -- streaming-pass kernels instantiated for float history
-// storage (one translation unit per storage type so that they compile in
-// parallel).
+// storage; every n-space operation runs on the FP32/INT pipes (MODE 2).
+// (One translation unit per storage type so that they compile in parallel.)
 #include "aa_passes.cuh"
 
 namespace aa {
 cudaError_t launch_pass_f32(const PassArgs &a, int nsm, int *grid_out, cudaStream_t stream) {
-  return launch_q<float>(a, nsm, grid_out, stream);
+  return launch_qm<float, 2>(a, nsm, grid_out, stream);
 }
 }  // namespace aa

@@ -1,10 +1,11 @@
-// aa_passes_f64.cu -- streaming-pass kernels instantiated for double history
-// storage (one translation unit per storage type so that they compile in
-// parallel).
+// aa_passes_f64.cu -- streaming-pass kernels instantiated for FP64 history
+// storage: the exact FP64 path and the variant with FP32-pipe dot products.
+// (One translation unit per storage type so that they compile in parallel.)
 #include "aa_passes.cuh"
 
 namespace aa {
 cudaError_t launch_pass_f64(const PassArgs &a, int nsm, int *grid_out, cudaStream_t stream) {
-  return launch_q<double>(a, nsm, grid_out, stream);
+  if (a.flags & 0x8u) return launch_qm<double, 1>(a, nsm, grid_out, stream);
+  return launch_qm<double, 0>(a, nsm, grid_out, stream);
 }
 }  // namespace aa

@@ -1,0 +1,97 @@
+"""Batched persistent form (many Bratu solves in one launch) against the
+oracle: ICWY, m = 10, FP32 history storage (oracle with the same storage
+rounding), stop at ||f||/||G(0)|| < 1e-8.
+
+Early iterates are compared with a capped iteration count (both sides
+return x_cap); the tolerance follows the precision-form tests (FP32 storage
+rounded at slightly different points: 1e-4 relative).  Converged solves must
+satisfy the stop rule when checked with the oracle's FP64 map, in an
+iteration count within 10 % of the oracle's.
+"""
+import numpy as np
+import pytest
+
+import aa_synth
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+SIDES = [8, 13, 20, 32, 17, 5, 40, 24, 9, 11]
+
+
+@pytest.fixture(scope="module")
+def aa():
+    import paper_2110_09667_gb300 as aa
+    aa.lib()
+    return aa
+
+
+def scale_of(ora, s, lam, src):
+    return float(np.linalg.norm(ora.g_bratu2d(s, lam, src, np.zeros(s * s))))
+
+
+def oracle_solve(ora, s, lam, src, max_iters, m=10):
+    O = ora.Oracle(s * s, m, "icwy", store_round=1)
+    sc = scale_of(ora, s, lam, src)
+    r = O.solve({"kind": "bratu2d", "s": s, "lam": lam, "src": src}, np.zeros(s * s),
+                max_iters=max_iters, tol=1e-8, scale=sc)
+    return r, sc
+
+
+def srcs_for(sides, seed):
+    out = []
+    for i, s in enumerate(sides):
+        out.append(aa_synth.uniform(seed + i, s * s) * 0.5 if i % 2 else np.zeros(s * s))
+    return out
+
+
+def test_batch_early_iterates(aa, ora):
+    sides = SIDES
+    lams = aa_synth.uniform(70, len(sides), 1.0, 6.0)
+    srcs = srcs_for(sides, 71)
+    B = aa.Batch(sides, lams, m=10, max_iters=15, src=np.concatenate(srcs))
+    B.solve()
+    it, rs, st = B.results()
+    for i, s in enumerate(sides):
+        r, _ = oracle_solve(ora, s, lams[i], srcs[i], 15)
+        assert it[i] == r["iters"], (i, it[i], r["iters"])  # 15, or earlier if converged
+        xg = B.solution(i)
+        assert np.linalg.norm(xg - r["x"]) <= 1e-4 * np.linalg.norm(r["x"]), (i, s)
+
+
+def test_batch_converges_like_oracle(aa, ora):
+    sides = SIDES
+    lams = aa_synth.uniform(72, len(sides), 1.0, 6.0)
+    srcs = srcs_for(sides, 73)
+    B = aa.Batch(sides, lams, m=10, max_iters=20000, src=np.concatenate(srcs))
+    B.solve()
+    it, rs, st = B.results()
+    for i, s in enumerate(sides):
+        r, sc = oracle_solve(ora, s, lams[i], srcs[i], 20000)
+        assert st[i] == 0 and r["status"] == 0, (i, st[i])
+        xg = B.solution(i)
+        res = np.linalg.norm(ora.g_bratu2d(s, lams[i], srcs[i], xg) - xg) / sc
+        assert res < 1.01e-8, (i, res)
+        assert abs(it[i] - r["iters"]) <= max(2, 0.1 * r["iters"]), (i, it[i], r["iters"])
+
+
+def test_batch_deterministic_and_warm_start(aa, ora):
+    sides = [30, 9, 21]
+    lams = np.array([2.0, 5.5, 4.0])
+    B = aa.Batch(sides, lams, m=10, max_iters=20000)
+    B.solve(block=256)
+    it0, _, _ = B.results()
+    x0 = [B.solution(i) for i in range(3)]
+    B.solve(block=256)
+    it1, _, _ = B.results()
+    assert np.array_equal(it0, it1)
+    assert all(np.array_equal(x0[i], B.solution(i)) for i in range(3))
+    # warm start: the converged solution needs (almost) no iterations; a
+    # wild guess for the second solve falls back to x_0 = 0 and still converges
+    guess = [x0[0], np.full(81, 1e3), x0[2]]
+    B.set_x0(np.concatenate(guess))
+    B.solve(block=128, ctas_per_sm=2)
+    it2, rs2, st2 = B.results()
+    assert it2[0] <= 1 and it2[2] <= 1 and st2[0] == 0 and st2[2] == 0
+    assert st2[1] == 0 and abs(it2[1] - it0[1]) <= max(2, 0.1 * it0[1])

@@ -226,3 +226,35 @@ def test_stagnation_breakdown_falls_back(aa, ora):
     A.step(dev(x), dev(g), xg)
     assert A.stats()["breakdowns"] == 1
     assert np.array_equal(xg.cpu().numpy(), xo2)
+
+
+# ------------------------------------- FP64 storage, FP32-pipe dot products
+
+@pytest.mark.parametrize("orth", VARIANTS)
+def test_step_parity_fp32_dots(aa, ora, orth):
+    """AA_FLAG_FP32_DOTS keeps the FP64 parity contract: the dot products
+    are formed on the FP32 pipe from (hi, lo) splits (error <= 2^-45 per
+    8-row group relative to sum |a_i b_i|) and accumulated in FP64."""
+    nx = ny = 64
+    b = aa_synth.jacobi2d_rhs(0, nx, ny)
+    Gmap = lambda x: ora.g_jacobi2d(nx, ny, 0.01, b, x)
+    out, _ = run_steps(aa, ora, Gmap, nx * ny, 5, orth, 21, flags=aa.FLAG_FP32_DOTS)
+    for i, (xo, xg, fo, fg) in enumerate(out):
+        assert abs(fg - fo) <= 1e-10 * abs(fo), (i, fo, fg)
+        assert np.linalg.norm(xg - xo) <= 1e-10 * np.linalg.norm(xo), (i, orth)
+
+
+@pytest.mark.parametrize("orth", VARIANTS)
+def test_qradd_fp32_dots(aa, ora, orth):
+    n, m = 4097, 4
+    V = aa_synth.uniform(60, (m + 4) * n).reshape(m + 4, n)
+    O = ora.Oracle(n, m, orth)
+    G = aa.Anderson(n, m, orth, flags=aa.FLAG_FP32_DOTS)
+    for j in range(m + 4):
+        O.qradd(V[j])
+        G.qradd(dev(V[j]))
+        Qo, Ro, _ = O.get_qr()
+        Qg, Rg, _ = G.get_qr()
+        tol = 1e-11 if orth != "dcgs2" else 1e-9
+        assert np.max(np.abs(Rg - Ro)) <= tol * np.abs(Ro).max(), (j, orth)
+        assert np.max(np.abs(Qg - Qo)) <= tol, (j, orth)
