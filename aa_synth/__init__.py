@@ -130,3 +130,15 @@ def matrix_with_condition(seed: int, n: int, m: int, kappa: float) -> np.ndarray
     V = householder_orthogonal(seed, m, m, stream=13)
     s = np.logspace(0.0, -math.log10(kappa), m)
     return (U * s) @ V.T
+
+
+def bratu_source_grid(c: np.ndarray, s: int, modes: int = 8) -> np.ndarray:
+    """Source f on the s x s interior grid (x_i = i h, h = 1/(s+1), index
+    p = j*s + i) for sine-mode coefficients c (modes x modes, row-major in
+    (k1, k2)): f(x, y) = sum_{k1,k2} c[k1,k2] / (k1^2 + k2^2) sin(k1 pi x) sin(k2 pi y)."""
+    k = np.arange(1, modes + 1)
+    x = np.arange(1, s + 1) / (s + 1.0)
+    S = np.sin(np.pi * np.outer(x, k))  # [s, modes]
+    W = np.asarray(c, dtype=np.float64).reshape(modes, modes) / (k[:, None] ** 2 + k[None, :] ** 2)
+    F = S @ W.T @ S.T  # F[j, i]: y index j, x index i
+    return F.reshape(-1)

@@ -244,10 +244,21 @@ int aa_batch_solve(aa_batch *b, int block, int ctas_per_sm, void *stream, double
 /* Per-solve iterations, final ||f||/||G(0)|| and status (0 converged, 1 cap
  * reached, AA_ENONFINITE) in input order; any pointer may be NULL. */
 int aa_batch_results(aa_batch *b, int32_t *iters, double *resid, int32_t *status);
+/* Per-solve flag (input order): 1 if the x_0 given by aa_batch_set_x0 was
+ * rejected by the residual test and the solve restarted from x_0 = 0. */
+int aa_batch_fallbacks(aa_batch *b, int32_t *fallback);
 /* Solution of solve idx (host, n_idx doubles). */
 int aa_batch_solution(aa_batch *b, int idx, double *x_host);
 /* Total arena rows (sum of n_i rounded up to 64 each). */
 int64_t aa_batch_rows(const aa_batch *b);
+/* Change the iteration cap of later aa_batch_solve calls. */
+int aa_batch_set_max_iters(aa_batch *b, int max_iters);
+
+/* e^u for n device doubles computed on the FP32 pipe (the exponential the
+ * batched Bratu map uses): range reduction by ln 2 and a degree-13 Taylor
+ * polynomial in (hi, lo) float arithmetic, relative error about
+ * (2|u| + 4) 2^-48 for |u| < 88.  out_dev may equal u_dev. */
+int aa_exp_fp32pipe(int64_t n, const double *u_dev, double *out_dev, void *stream);
 
 /* Message for the last error on this thread. */
 const char *aa_last_error(void);

@@ -246,8 +246,11 @@ def _batch_lib():
         L.aa_batch_solve.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, _dp]
         L.aa_batch_results.argtypes = [C.c_void_p, C.POINTER(C.c_int32), _dp, C.POINTER(C.c_int32)]
         L.aa_batch_solution.argtypes = [C.c_void_p, C.c_int, _dp]
+        L.aa_batch_fallbacks.argtypes = [C.c_void_p, C.POINTER(C.c_int32)]
         L.aa_batch_rows.argtypes = [C.c_void_p]
         L.aa_batch_rows.restype = C.c_int64
+        L.aa_batch_set_max_iters.argtypes = [C.c_void_p, C.c_int]
+        L.aa_exp_fp32pipe.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]
         L._batch_ready = True
     return L
 
@@ -308,6 +311,12 @@ class Batch:
                                              stt.ctypes.data_as(C.POINTER(C.c_int32))))
         return it, rs, stt
 
+    def fallbacks(self):
+        import numpy as np
+        fb = np.zeros(self.count, dtype=np.int32)
+        _check(_batch_lib().aa_batch_fallbacks(self._h, fb.ctypes.data_as(C.POINTER(C.c_int32))))
+        return fb
+
     def solution(self, i: int):
         import numpy as np
         x = np.zeros(int(self.sides[i]) ** 2)
@@ -316,3 +325,13 @@ class Batch:
 
     def rows(self) -> int:
         return int(_batch_lib().aa_batch_rows(self._h))
+
+    def set_max_iters(self, k: int):
+        _check(_batch_lib().aa_batch_set_max_iters(self._h, int(k)))
+
+
+def exp_fp32pipe(u):
+    """e^u on the FP32 pipe (aa_exp_fp32pipe) for an FP64 CUDA tensor."""
+    out = u.new_empty(u.shape)
+    _check(_batch_lib().aa_exp_fp32pipe(u.numel(), _ptr(u), _ptr(out), _stream()))
+    return out

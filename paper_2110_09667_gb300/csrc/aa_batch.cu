@@ -35,7 +35,7 @@ namespace {
 using aa::F2;
 
 constexpr int BM = 16;             // largest history depth of the batched form
-constexpr int BNDOT = 3 + 3 * BM;  // dot products of pass A at most
+constexpr int BNDOT = 3 + 3 * BM;  // dot products of pass A at most (state arrays)
 
 struct Solve {
   int64_t off;     // first row in the arena
@@ -209,8 +209,10 @@ __device__ void finalize_b(SState &st, int m, int k, double rho, double vf, doub
   if (st.c == m && st.pend == 0) prepare_delete_b(st, m, lane);
 }
 
-template <int NT>
-__global__ void __launch_bounds__(NT) batch_kernel(BArgs a) {
+// MB: history-depth bucket (m <= MB) -- sizes the per-thread accumulators.
+template <int NT, int MB>
+__global__ void __launch_bounds__(NT, NT <= 128 ? 4 : (NT <= 256 ? 2 : 1)) batch_kernel(BArgs a) {
+  constexpr int ND = 3 + 3 * MB;
   __shared__ SState st;
   __shared__ double wbuf[(NT / 32) * BNDOT];
   __shared__ float cfr[4 * BM], cfc[2 * BM], cfg[2 * BM], cfv[2];
@@ -261,18 +263,18 @@ __global__ void __launch_bounds__(NT) batch_kernel(BArgs a) {
         __syncthreads();
       }
       const int nd = (it == 0) ? 1 : 3 + 3 * k - (k > 0 ? 1 : 0);
-      float aS[BNDOT], aC[BNDOT];
+      float aS[ND], aC[ND];
 #pragma unroll
-      for (int d = 0; d < BNDOT; ++d) aS[d] = aC[d] = 0.f;
-      for (int64_t r = tid; r < n; r += NT) {
-        const int64_t j = r / s, i = r - j * s;
+      for (int d = 0; d < ND; ++d) aS[d] = aC[d] = 0.f;
+      for (int r = tid; r < (int)n; r += NT) {
+        const int j = r / s, i = r - j * s;
         const double x = Xc[r];
         const double w = i > 0 ? Xc[r - 1] : 0.0;
         const double e = i < s - 1 ? Xc[r + 1] : 0.0;
         const double so = j > 0 ? Xc[r - s] : 0.0;
         const double no = j < s - 1 ? Xc[r + s] : 0.0;
-        const double rhs = lam * exp(x) + (src ? src[r] : 0.0);
-        const double g = ((w + e) + (so + no) + h2 * rhs) / 4.0;
+        const double rhs = lam * aa::exp_df(x) + (src ? src[r] : 0.0);
+        const double g = ((w + e) + (so + no) + h2 * rhs) * 0.25;
         const double f = g - x;
         const F2 f2 = aa::d2f2(f);
         float p, q;
@@ -294,14 +296,14 @@ __global__ void __launch_bounds__(NT) batch_kernel(BArgs a) {
         aa::prod_ff(d2, f2, p, q);
         aa::acc_add(aS[2], aC[2], p, q);
         if (k == 0) a.Q[off + r] = aa::d2f_rn(df);
-        float qv[BM];
+        float qv[MB];
 #pragma unroll
-        for (int jj = 0; jj < BM; ++jj)
+        for (int jj = 0; jj < MB; ++jj)
           if (jj < c) qv[jj] = a.Q[(int64_t)jj * a.N + off + r];
         if (del) {
           F2 wv{qv[0], 0.f};
 #pragma unroll
-          for (int jj = 0; jj < BM - 1; ++jj) {
+          for (int jj = 0; jj < MB - 1; ++jj) {
             if (jj < m - 1) {
               const float u = qv[jj + 1];
               const F2 k1{cfr[4 * jj], cfr[4 * jj + 1]}, k2{cfr[4 * jj + 2], cfr[4 * jj + 3]};
@@ -321,25 +323,25 @@ __global__ void __launch_bounds__(NT) batch_kernel(BArgs a) {
         }
         // Q'^T f (rhs), Q'^T df (R column), Q'^T q'_{k-1} (delayed T row)
 #pragma unroll
-        for (int jj = 0; jj < BM; ++jj)
+        for (int jj = 0; jj < MB; ++jj)
           if (jj < k) {
             aa::prod_f(f2, qv[jj], p, q);
             aa::acc_add(aS[3 + jj], aC[3 + jj], p, q);
             aa::prod_f(d2, qv[jj], p, q);
-            aa::acc_add(aS[3 + BM + jj], aC[3 + BM + jj], p, q);
+            aa::acc_add(aS[3 + MB + jj], aC[3 + MB + jj], p, q);
             if (jj + 1 < k) {
               p = __fmul_rn(qv[jj], qv[k - 1]);
               q = __fmaf_rn(qv[jj], qv[k - 1], -p);
-              aa::acc_add(aS[3 + 2 * BM + jj], aC[3 + 2 * BM + jj], p, q);
+              aa::acc_add(aS[3 + 2 * MB + jj], aC[3 + 2 * MB + jj], p, q);
             }
           }
       }
       (void)nd;
       {
-        double vals[BNDOT];
+        double vals[ND];
 #pragma unroll
-        for (int d = 0; d < BNDOT; ++d) vals[d] = aa::f2d(aS[d]) + aa::f2d(aC[d]);
-        block_reduce<NT>(vals, BNDOT, wbuf, st);
+        for (int d = 0; d < ND; ++d) vals[d] = aa::f2d(aS[d]) + aa::f2d(aC[d]);
+        block_reduce<NT>(vals, ND, wbuf, st);
       }
       // ---- warp 0: stop test, R column, T row, projection coefficients
       if (warp == 0) {
@@ -380,10 +382,10 @@ __global__ void __launch_bounds__(NT) batch_kernel(BArgs a) {
           st.vscale = st.dfn2 > 0.0 ? 1.0 / sqrt(st.dfn2) : 1.0;
           if (k > 0) {
             for (int l = 0; l + 1 < k; ++l)
-              st.T[(k - 1) * BM + l] = st.sig[l] * st.sig[k - 1] * st.red[3 + 2 * BM + l];
+              st.T[(k - 1) * BM + l] = st.sig[l] * st.sig[k - 1] * st.red[3 + 2 * MB + l];
             for (int l = k - 1; l < BM; ++l) st.T[(k - 1) * BM + l] = (l == k - 1) ? 1.0 : 0.0;
             for (int jj = 0; jj < k; ++jj) {
-              double v = st.sig[jj] * st.red[3 + BM + jj];
+              double v = st.sig[jj] * st.red[3 + MB + jj];
               for (int l = 0; l < jj; ++l) v -= st.T[jj * BM + l] * st.rcol[l];
               st.rcol[jj] = v;
             }
@@ -420,7 +422,7 @@ __global__ void __launch_bounds__(NT) batch_kernel(BArgs a) {
         for (int64_t r = tid; r < n; r += NT) {
           F2 acc = aa::d2f2(DF[r]);
 #pragma unroll
-          for (int jj = 0; jj < BM; ++jj)
+          for (int jj = 0; jj < MB; ++jj)
             if (jj < k) acc = aa::df_axpy_f(acc, F2{cfc[2 * jj], cfc[2 * jj + 1]},
                                             a.Q[(int64_t)jj * a.N + off + r]);
           float p, q;
@@ -460,7 +462,7 @@ __global__ void __launch_bounds__(NT) batch_kernel(BArgs a) {
         }
         F2 acc = aa::d2f2(GP[r]);
 #pragma unroll
-        for (int jj = 0; jj < BM; ++jj)
+        for (int jj = 0; jj < MB; ++jj)
           if ((gmask >> jj) & 1u)
             acc = aa::df_axpy_f(acc, F2{cfg[2 * jj], cfg[2 * jj + 1]},
                                 a.DG[(int64_t)jj * a.N + off + r]);
@@ -612,7 +614,10 @@ extern "C" void aa_batch_destroy(aa_batch *b) {
 
 template <int NT>
 static cudaError_t launch_batch(const BArgs &a, int grid, cudaStream_t s) {
-  batch_kernel<NT><<<grid, NT, 0, s>>>(a);
+  if (a.m <= 4) batch_kernel<NT, 4><<<grid, NT, 0, s>>>(a);
+  else if (a.m <= 8) batch_kernel<NT, 8><<<grid, NT, 0, s>>>(a);
+  else if (a.m <= 12) batch_kernel<NT, 12><<<grid, NT, 0, s>>>(a);
+  else batch_kernel<NT, 16><<<grid, NT, 0, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -712,6 +717,16 @@ extern "C" int aa_batch_results(aa_batch *b, int32_t *iters, double *resid, int3
   return AA_OK;
 }
 
+extern "C" int aa_batch_fallbacks(aa_batch *b, int32_t *fallback) {
+  if (!b || !fallback) return AA_EINVAL;
+  std::vector<Result> r(b->count);
+  if (cudaMemcpy(r.data(), b->dres, sizeof(Result) * b->count, cudaMemcpyDeviceToHost) !=
+      cudaSuccess)
+    return AA_ECUDA;
+  for (int i = 0; i < b->count; ++i) fallback[i] = r[i].fallback;
+  return AA_OK;
+}
+
 extern "C" int aa_batch_solution(aa_batch *b, int idx, double *x_host) {
   if (!b || idx < 0 || idx >= b->count || !x_host) return AA_EINVAL;
   for (const Solve &S : b->hsolves)
@@ -725,6 +740,33 @@ extern "C" int aa_batch_solution(aa_batch *b, int idx, double *x_host) {
 }
 
 extern "C" int64_t aa_batch_rows(const aa_batch *b) { return b ? b->N : 0; }
+
+extern "C" int aa_batch_set_max_iters(aa_batch *b, int max_iters) {
+  if (!b || max_iters < 1) return AA_EINVAL;
+  if (b->max_iters != max_iters) {
+    b->max_iters = max_iters;
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->gexec = nullptr;
+    b->graph = nullptr;
+  }
+  return AA_OK;
+}
+
+namespace {
+__global__ void exp_kernel(int64_t n, const double *__restrict__ u, double *__restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = aa::exp_df(u[i]);
+}
+}  // namespace
+
+extern "C" int aa_exp_fp32pipe(int64_t n, const double *u, double *out, void *stream) {
+  if (n < 1 || !u || !out) return AA_EINVAL;
+  const int64_t g = (n + 255) / 256;
+  exp_kernel<<<(int)(g > 4096 ? 4096 : g), 256, 0, (cudaStream_t)stream>>>(n, u, out);
+  return cudaGetLastError() == cudaSuccess ? AA_OK : AA_ECUDA;
+}
 
 extern "C" int aa_batch_set_x0(aa_batch *b, const double *x0_host) {
   if (!b) return AA_EINVAL;

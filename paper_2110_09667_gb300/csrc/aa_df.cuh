@@ -129,4 +129,65 @@ __device__ __forceinline__ F2 df_axpy_ff(float u, F2 c, F2 a) {
   return fast_two_sum(s, t);
 }
 
+// (a + b) for two (hi, lo) pairs, normalised.
+__device__ __forceinline__ F2 df_add(F2 a, F2 b) {
+  float s, t;
+  two_sum(a.h, b.h, s, t);
+  t = __fadd_rn(t, __fadd_rn(a.l, b.l));
+  return fast_two_sum(s, t);
+}
+
+// c * a + b for (hi, lo) pairs (one Horner step), normalised.
+__device__ __forceinline__ F2 df_mad(F2 c, F2 a, F2 b) {
+  float p, e, s, t;
+  prod_ff(c, a, p, e);
+  two_sum(b.h, p, s, t);
+  t = __fadd_rn(t, __fadd_rn(b.l, e));
+  return fast_two_sum(s, t);
+}
+
+// e^u for a double u on the FP32 pipe.  The split of u and the rounding of
+// the reduced argument's low part each carry an absolute error of up to
+// |u| 2^-48, which becomes a relative error of e^u, so the result is accurate
+// to about (2|u| + 4) 2^-48 relative.
+// Range reduction u = k ln2 + r with |r| <= ln2/2, ln2 = L1 + L2 + L3 (L1
+// has a short significand, so k L1 is exact for |k| < 128); then
+// e^r = sum_{j=0}^{13} r^j / j! by Horner's rule in (hi, lo) arithmetic
+// (truncation error below 0.35^14/14! < 2^-52); finally the exact scaling by
+// 2^k.  Returns +inf above the float range, 0 below it.
+__device__ __forceinline__ double exp_df(double u) {
+  // 1/j!, j = 0..13, as (hi, lo) float pairs (hi = 1/j! rounded to float,
+  // lo = the rounded remainder)
+  const float C[14][2] = {{1.0f, 0.0f},
+                          {1.0f, 0.0f},
+                          {0.5f, 0.0f},
+                          {0.1666666716337204f, -4.967053879312289e-09f},
+                          {0.0416666679084301f, -1.2417634698280722e-09f},
+                          {0.008333333767950535f, -4.34617203337595e-10f},
+                          {0.0013888889225199819f, -3.3631094437103215e-11f},
+                          {0.00019841270113829523f, -2.725596874933456e-12f},
+                          {2.4801587642286904e-05f, -3.40699609366682e-13f},
+                          {2.7557318844628753e-06f, 3.793571224297229e-14f},
+                          {2.755731998149713e-07f, -7.575112209051195e-15f},
+                          {2.5052107943679403e-08f, 4.4176230446483665e-16f},
+                          {2.0876755879584152e-09f, 1.1082839147459852e-16f},
+                          {1.6059044372074283e-10f, -5.352526511562726e-18f}};
+  const float L1 = 0x1.62e4p-1f, L2 = 0x1.7f7d1cp-20f, L3 = 0x1.ef357ap-45f;
+  const F2 x = d2f2(u);
+  const float kf = rintf(__fmul_rn(x.h, 1.44269502f));
+  if (kf > 127.f) return __longlong_as_double(0x7ff0000000000000LL);
+  if (kf < -125.f) return 0.0;
+  const float r0 = __fmaf_rn(-kf, L1, x.h);  // exact
+  const float p = __fmul_rn(kf, L2), pe = __fmaf_rn(kf, L2, -p);
+  float s, t;
+  two_sum(r0, -p, s, t);
+  const float low = __fadd_rn(__fsub_rn(t, pe), __fsub_rn(x.l, __fmul_rn(kf, L3)));
+  const F2 r = fast_two_sum(s, low);
+  F2 P{C[13][0], C[13][1]};
+#pragma unroll
+  for (int j = 12; j >= 0; --j) P = df_mad(P, r, F2{C[j][0], C[j][1]});
+  const float sc = __int_as_float(((int)kf + 127) << 23);
+  return f2d(__fmul_rn(P.h, sc)) + f2d(__fmul_rn(P.l, sc));
+}
+
 }  // namespace aa

@@ -1,0 +1,244 @@
+"""Learned warm start: an MLP maps Bratu parameters (lambda, source modes) to
+an initial guess x_0 for the Anderson solve.
+
+Network: 65 -> 1024 -> 1024 -> s*s (GELU after the two hidden layers), BF16
+weights and activations, FP32 accumulation, FP32 master weights and Adam
+moments.  Every arithmetic step -- the GEMMs (aa_gemm_bf16_nt, tensor
+cores), bias/GELU epilogues, GELU derivative, MSE, bias gradients, Adam --
+runs in libaa's kernels; this module only allocates device memory (torch)
+and sequences the calls.  Training data are converged AA(10) solutions from
+the batched form (aa_batch_*), and the solve that uses the prediction falls
+back to x_0 = 0 whenever ||G(x_0) - x_0|| is not below ||G(0)||.
+"""
+from __future__ import annotations
+
+import ctypes as C  # noqa: N812
+
+import numpy as np
+
+from . import AAError, _check, _stream, lib
+
+IN_DIM = 65
+IN_PAD = 72  # GEMM needs K % 8 == 0
+HIDDEN = 1024
+
+
+def _L():
+    L = lib()
+    if not getattr(L, "_mlp_ready", False):
+        vp, i32, i64, f32 = C.c_void_p, C.c_int, C.c_int64, C.c_float
+        L.aa_gemm_bf16_nt.argtypes = [i32, i32, i32, vp, i32, vp, i32, vp, i32, vp, vp, i32, i32, vp]
+        L.aa_transpose_bf16.argtypes = [i32, i32, vp, i32, vp, i32, vp]
+        L.aa_gelu_bwd.argtypes = [i64, vp, vp, vp]
+        L.aa_mse.argtypes = [i64, vp, vp, f32, vp, vp, i32, vp]
+        L.aa_colsum_bf16.argtypes = [i32, i32, vp, i32, vp, vp]
+        L.aa_adam.argtypes = [i64, vp, vp, vp, vp, vp, f32, f32, f32, f32, i32, f32, vp]
+        L.aa_f32_to_bf16.argtypes = [i64, vp, vp, vp]
+        L._mlp_ready = True
+    return L
+
+
+def _p(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+EPI_BIAS, EPI_GELU, EPI_BF16, EPI_PRE = 1, 2, 4, 8
+
+
+def gemm_nt(A, B, C_out, *, bias=None, pre=None, epi=0):
+    """C = A B^T (A: [M, K] bf16, B: [N, K] bf16)."""
+    M, K = A.shape
+    N = B.shape[0]
+    rc = _L().aa_gemm_bf16_nt(M, N, K, _p(A), A.stride(0), _p(B), B.stride(0), _p(C_out),
+                              C_out.stride(0), _p(bias), _p(pre),
+                              pre.stride(0) if pre is not None else 0, epi, _stream())
+    if rc != 0:
+        raise AAError(rc, "aa_gemm_bf16_nt")
+
+
+def transpose(X, out):
+    r, c = X.shape
+    rc = _L().aa_transpose_bf16(r, c, _p(X), X.stride(0), _p(out), out.stride(0), _stream())
+    if rc != 0:
+        raise AAError(rc, "aa_transpose_bf16")
+    return out
+
+
+class MLP:
+    """65 -> hidden -> hidden -> out MLP trained with the library's kernels."""
+
+    def __init__(self, out_dim: int, hidden: int = HIDDEN, seed: int = 0, device="cuda"):
+        import torch
+
+        import aa_synth
+        self.torch = torch
+        self.dims = [IN_PAD, hidden, hidden, out_dim]
+        self.params = []  # (W master fp32 [out, in], W bf16, b fp32)
+        for li in range(3):
+            fi, fo = self.dims[li], self.dims[li + 1]
+            fan_in = IN_DIM if li == 0 else fi
+            std = np.sqrt(2.0 / fan_in) if li < 2 else np.sqrt(1.0 / fan_in)
+            w = aa_synth.normal(seed * 10 + li, fo * fi, stream=200 + li).reshape(fo, fi) * std
+            if li == 0:
+                w[:, IN_DIM:] = 0.0
+            if li == 2:
+                # The output layer starts at zero: its rows then only ever hold
+                # combinations of training-target patterns, so predictions carry no
+                # pixel-level noise (the Jacobi residual that gates a warm start
+                # amplifies such noise like a discrete Laplacian).
+                w[:] = 0.0
+            W = torch.from_numpy(w.astype(np.float32)).to(device)
+            Wb = torch.empty(fo, fi, dtype=torch.bfloat16, device=device)
+            _check(_L().aa_f32_to_bf16(W.numel(), _p(W), _p(Wb), _stream()))
+            b = torch.zeros(fo, dtype=torch.float32, device=device)
+            self.params.append([W, Wb, b])
+        self.opt = [[torch.zeros_like(W), torch.zeros_like(W), torch.zeros_like(b),
+                     torch.zeros_like(b)] for W, _, b in self.params]
+        self.step_n = 0
+        self._ws = {}
+
+    def _buf(self, name, shape, dtype):
+        t = self._ws.get(name)
+        if t is None or tuple(t.shape) != tuple(shape) or t.dtype != dtype:
+            t = self.torch.empty(*shape, dtype=dtype, device="cuda")
+            self._ws[name] = t
+        return t
+
+    def forward(self, X):
+        """X: [B, IN_PAD] bf16 -> Y [B, out] fp32 (keeps activations for backward)."""
+        torch = self.torch
+        Bn = X.shape[0]
+        acts = [X]
+        pres = []
+        for li, (W, Wb, b) in enumerate(self.params):
+            fo = self.dims[li + 1]
+            if li < 2:
+                pre = self._buf(f"pre{li}", (Bn, fo), torch.float32)
+                H = self._buf(f"h{li}", (Bn, fo), torch.bfloat16)
+                gemm_nt(acts[-1], Wb, H, bias=b, pre=pre, epi=EPI_BIAS | EPI_GELU | EPI_BF16 | EPI_PRE)
+                acts.append(H)
+                pres.append(pre)
+            else:
+                Y = self._buf("y", (Bn, fo), torch.float32)
+                gemm_nt(acts[-1], Wb, Y, bias=b, epi=EPI_BIAS)
+        self._acts, self._pres = acts, pres
+        return Y
+
+    def loss_and_grad(self, Y, T):
+        """MSE loss (host float) and dY (bf16) for targets T (fp32)."""
+        torch = self.torch
+        dY = self._buf("dy", tuple(Y.shape), torch.bfloat16)
+        nb = 1024
+        bl = self._buf("bl", (nb,), torch.float64)
+        _check(_L().aa_mse(Y.numel(), _p(Y), _p(T), 1.0 / Y.numel(), _p(dY), _p(bl), nb, _stream()))
+        return float(bl.cpu().numpy().sum()) / Y.numel(), dY
+
+    def backward(self, dY):
+        """Gradients (fp32) of every parameter from dY [B, out] (bf16)."""
+        torch = self.torch
+        grads = [None, None, None]
+        dH = dY
+        for li in (2, 1, 0):
+            W, Wb, b = self.params[li]
+            fo, fi = W.shape
+            Bn = dH.shape[0]
+            Xin = self._acts[li]
+            # dW = dH^T X  ->  NT GEMM of dH^T [fo, B] and X^T [fi, B]
+            dHt = transpose(dH, self._buf(f"dht{li}", (fo, Bn), torch.bfloat16))
+            Xt = transpose(Xin, self._buf(f"xt{li}", (fi, Bn), torch.bfloat16))
+            gW = self._buf(f"gw{li}", (fo, fi), torch.float32)
+            gemm_nt(dHt, Xt, gW)
+            gb = self._buf(f"gb{li}", (fo,), torch.float32)
+            _check(_L().aa_colsum_bf16(Bn, fo, _p(dH), dH.stride(0), _p(gb), _stream()))
+            grads[li] = (gW, gb)
+            if li > 0:
+                # dX = dH W  ->  NT GEMM of dH [B, fo] and W^T [fi, fo]
+                Wt = transpose(Wb, self._buf(f"wt{li}", (fi, fo), torch.bfloat16))
+                dX = self._buf(f"dx{li}", (Bn, fi), torch.bfloat16)
+                gemm_nt(dH, Wt, dX, epi=EPI_BF16)
+                _check(_L().aa_gelu_bwd(dX.numel(), _p(self._pres[li - 1]), _p(dX), _stream()))
+                dH = dX
+        return grads
+
+    def adam_step(self, grads, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, wd=0.0):
+        self.step_n += 1
+        for (W, Wb, b), (gW, gb), (mW, vW, mb, vb) in zip(self.params, grads, self.opt):
+            _check(_L().aa_adam(W.numel(), _p(W), _p(Wb), _p(gW), _p(mW), _p(vW), lr, beta1, beta2,
+                                eps, self.step_n, wd, _stream()))
+            _check(_L().aa_adam(b.numel(), _p(b), None, _p(gb), _p(mb), _p(vb), lr, beta1, beta2,
+                                eps, self.step_n, 0.0, _stream()))
+
+
+def features(lams, coeffs):
+    """MLP inputs: [(lambda - 3.5) / 1.5, c_1..c_64, zero padding] as bf16-ready fp32."""
+    lams = np.asarray(lams, dtype=np.float64)
+    X = np.zeros((len(lams), IN_PAD), dtype=np.float32)
+    X[:, 0] = (lams - 3.5) / 1.5
+    X[:, 1:IN_DIM] = np.asarray(coeffs, dtype=np.float32)
+    return X
+
+
+# ------------------------------------------------------------------ pipeline
+
+def instances(seeds, s: int):
+    """Parametric Bratu instances for the given seeds: (lambdas, coeffs [N, 64], sources [N, s*s])."""
+    import aa_synth
+    lams, cs, srcs = [], [], []
+    for sd in seeds:
+        lam, c = aa_synth.bratu_source_params(int(sd))
+        lams.append(lam)
+        cs.append(c)
+        srcs.append(aa_synth.bratu_source_grid(c, s))
+    return np.array(lams), np.array(cs), np.array(srcs)
+
+
+def solve_batch(lams, srcs, s: int, *, x0=None, m: int = 10, max_iters: int = 100000,
+                block: int = 256, ctas_per_sm: int = 2):
+    """Batched AA(m) solves; returns (solutions [N, s*s], iterations, status, ms, fallback flags)."""
+    from . import Batch
+    n = len(lams)
+    B = Batch(np.full(n, s, dtype=np.int64), lams, m=m, max_iters=max_iters,
+              src=np.concatenate(list(srcs)))
+    if x0 is not None:
+        B.set_x0(np.asarray(x0, dtype=np.float64).reshape(-1))
+    ms = B.solve(block, ctas_per_sm)
+    it, rs, st = B.results()
+    fb = B.fallbacks()
+    U = np.stack([B.solution(i) for i in range(n)])
+    B.close()
+    return U, it, st, ms, fb
+
+
+def train(net, X, U, *, epochs: int = 30, batch: int = 128, lr: float = 1e-3, seed: int = 0,
+          log=None):
+    """Mini-batch Adam on MSE(net(X), U); X fp32 [N, IN_PAD], U fp32 [N, out]."""
+    import torch
+    N = X.shape[0]
+    Xd = torch.from_numpy(X).cuda().to(torch.bfloat16)
+    Ud = torch.from_numpy(U.astype(np.float32)).cuda()
+    rng = np.random.default_rng(seed)
+    hist = []
+    for ep in range(epochs):
+        perm = rng.permutation(N)
+        tot = 0.0
+        for b0 in range(0, N - batch + 1, batch):
+            idx = torch.from_numpy(perm[b0:b0 + batch]).cuda()
+            xb = Xd.index_select(0, idx)
+            yb = Ud.index_select(0, idx)
+            Y = net.forward(xb)
+            loss, dY = net.loss_and_grad(Y, yb)
+            net.adam_step(net.backward(dY), lr=lr)
+            tot += loss
+        hist.append(tot / max(1, N // batch))
+        if log:
+            log(f"epoch {ep} loss {hist[-1]:.3e}")
+    return hist
+
+
+def predict(net, X, batch: int = 128):
+    import torch
+    out = []
+    for b0 in range(0, X.shape[0], batch):
+        xb = torch.from_numpy(X[b0:b0 + batch]).cuda().to(torch.bfloat16)
+        out.append(net.forward(xb).float().cpu().numpy().copy())
+    return np.concatenate(out)
