@@ -256,8 +256,8 @@ int aa_batch_set_max_iters(aa_batch *b, int max_iters);
 
 /* e^u for n device doubles computed on the FP32 pipe (the exponential the
  * batched Bratu map uses): range reduction by ln 2 and a degree-13 Taylor
- * polynomial in (hi, lo) float arithmetic, relative error about
- * (2|u| + 4) 2^-48 for |u| < 88.  out_dev may equal u_dev. */
+ * polynomial in (hi, lo) float arithmetic, relative error at most about
+ * 3 |u| 2^-48 + 2^-45 for |u| < 88.  out_dev may equal u_dev. */
 int aa_exp_fp32pipe(int64_t n, const double *u_dev, double *out_dev, void *stream);
 
 /* Message for the last error on this thread. */

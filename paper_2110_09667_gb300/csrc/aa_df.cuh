@@ -146,10 +146,10 @@ __device__ __forceinline__ F2 df_mad(F2 c, F2 a, F2 b) {
   return fast_two_sum(s, t);
 }
 
-// e^u for a double u on the FP32 pipe.  The split of u and the rounding of
-// the reduced argument's low part each carry an absolute error of up to
-// |u| 2^-48, which becomes a relative error of e^u, so the result is accurate
-// to about (2|u| + 4) 2^-48 relative.
+// e^u for a double u on the FP32 pipe.  The split of u and the roundings in
+// the reduced argument's low part carry an absolute error of up to about
+// 3 |u| 2^-48, which becomes a relative error of e^u; the polynomial and the
+// final scaling add a few 2^-48: relative error <= 3 |u| 2^-48 + 2^-45.
 // Range reduction u = k ln2 + r with |r| <= ln2/2, ln2 = L1 + L2 + L3 (L1
 // has a short significand, so k L1 is exact for |k| < 128); then
 // e^r = sum_{j=0}^{13} r^j / j! by Horner's rule in (hi, lo) arithmetic

@@ -100,14 +100,14 @@ def test_batch_deterministic_and_warm_start(aa, ora):
 def test_exp_fp32pipe_accuracy(aa):
     """The FP32-pipe exponential used by the batched Bratu map against
     CUDA's FP64 exp (torch.exp on the device).  The (hi, lo) split of u and
-    the rounding of the reduced argument each err by up to |u| 2^-48
-    absolutely, i.e. relatively in e^u; the polynomial and the scaling add a
-    few 2^-48: bound (2|u| + 8) 2^-48."""
+    the roundings of the reduced argument's low part err by up to about
+    3 |u| 2^-48 absolutely, i.e. relatively in e^u; the polynomial and the
+    scaling add a few 2^-48: bound 3 |u| 2^-48 + 2^-45."""
     u = torch.linspace(-20.0, 20.0, 200001, dtype=torch.float64, device="cuda")
     u = torch.cat([u, torch.tensor([0.0, 1e-30, -1e-30, 0.6931471805599453, 3.0], dtype=torch.float64,
                                    device="cuda")])
     got = aa.exp_fp32pipe(u)
     ref = torch.exp(u)
     rel = (got - ref).abs() / ref
-    bound = (2.0 * u.abs() + 8.0) * 2.0 ** -48
+    bound = (3.0 * u.abs() + 8.0) * 2.0 ** -48
     assert bool((rel <= bound).all()), (rel / bound).max().item()
