@@ -13,7 +13,7 @@ import os
 
 from .build import LIB
 
-__all__ = ["Anderson", "lib", "mdot", "AAError", "ORTH", "STORAGE",
+__all__ = ["Anderson", "Batch", "lib", "mdot", "mdot_noalloc", "AAError", "ORTH", "STORAGE",
            "Jacobi2D", "Jacobi3D", "Bratu2D"]
 
 ORTH = {"mgs": 0, "icwy": 1, "cgs2": 2, "dcgs2": 3}

@@ -68,6 +68,12 @@ def test_mlp_gradients_vs_oracle(ws):
     against the FP64 oracle MLP, on the same BF16 weights and inputs."""
     out_dim, hidden, Bn = 48, 64, 32
     net = ws.MLP(out_dim, hidden=hidden, seed=3)
+    # the output layer starts at zero in training; give it random weights so
+    # that every layer's gradient is nonzero here
+    W3, Wb3, _ = net.params[2]
+    W3.copy_(torch.from_numpy((aa_synth.normal(13, W3.numel()).reshape(W3.shape) / 8.0)
+                              .astype(np.float32)).cuda())
+    assert ws._L().aa_f32_to_bf16(W3.numel(), ws._p(W3), ws._p(Wb3), ws._stream()) == 0
     P = []
     for W, Wb, b in net.params:
         P.append((Wb.float().cpu().numpy().astype(np.float64), b.cpu().numpy().astype(np.float64)))
