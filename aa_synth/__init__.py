@@ -142,3 +142,14 @@ def bratu_source_grid(c: np.ndarray, s: int, modes: int = 8) -> np.ndarray:
     W = np.asarray(c, dtype=np.float64).reshape(modes, modes) / (k[:, None] ** 2 + k[None, :] ** 2)
     F = S @ W.T @ S.T  # F[j, i]: y index j, x index i
     return F.reshape(-1)
+
+
+def mixture_samples(seed: int, count: int, alpha=(0.3, 0.3, 0.4), mu=(0.0, 0.5, 1.0),
+                    sigma=(1.0, 1.0, 1.0)) -> np.ndarray:
+    """count draws from the univariate normal mixture sum_i alpha_i N(mu_i, sigma_i^2):
+    the component by inverting the cumulative proportions on a uniform, the value
+    by a standard normal scaled and shifted."""
+    u = uniform(seed, count, 0.0, 1.0, stream=7)
+    z = normal(seed, count, stream=8)
+    comp = np.searchsorted(np.cumsum(alpha)[:-1], u, side="right")
+    return np.asarray(mu, dtype=np.float64)[comp] + np.asarray(sigma, dtype=np.float64)[comp] * z

@@ -285,7 +285,9 @@ def run_ours(args, ws, rank, local):
                 traffic = tr[key]["bytes_per_launch_full_n"]
         except Exception:
             traffic = None
-    if fp64_frac > hbm_frac:
+    # Only the exact-FP64 mode runs its row arithmetic on the FP64 pipe; the
+    # FP32-history and FP32-dot modes do it on the FP32/INT pipes (HBM-bound form).
+    if args.storage == "fp64" and not args.fp32_dots and fp64_frac > hbm_frac:
         roof = {"bound": "alu", "achieved": round(tflops, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
                 "unit": "TFLOP/s", "frac": round(fp64_frac, 4), "traffic": traffic,
                 "peak_source": "FP64 pipe: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (derived)",
@@ -307,6 +309,7 @@ def run_ours(args, ws, rank, local):
     if not args.no_e2e:
         e2e = run_e2e(args, A, gfn, Pp, n, dev, stream, one_step_state=(x, xn, g))
     wall = run_wall_to_tol(aa, args, dev) if (rank == 0 and not args.no_wall) else None
+    startup = run_startup(A, one_step, x, stream, args.m)
     if ws > 1:
         import torch.distributed as dist
         dist.barrier()
@@ -348,10 +351,32 @@ def run_ours(args, ws, rank, local):
         "clocks": ck,
         "e2e": e2e,
         "wall_to_1e-8": wall,
+        "startup": startup,
     }
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(args)
     return line
+
+
+def run_startup(A, one_step, x, stream, m):
+    """The start-up phase (Sec. 4.1): cumulative time of the m iterations
+    that fill the history from x0 = 0, after a reset, with CUDA events on the
+    launching stream; G is included, and the AA passes alone are given too."""
+    import torch
+    A.reset()
+    x.zero_()
+    torch.cuda.synchronize()
+    pt0 = A.pass_times()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(m):
+        one_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    pt1 = A.pass_times()
+    aa_ms = sum(t - pt0.get(kd, (0.0, 0))[0] for kd, (t, _) in pt1.items())
+    return {"iterations": m, "ms": round(e0.elapsed_time(e1), 3), "aa_passes_ms": round(aa_ms, 3)}
 
 
 def run_e2e(args, A, gfn, Pp, n, dev, stream, one_step_state):

@@ -51,3 +51,28 @@ def heat(N: int, term: int):
 def bratu(N: int, lam: float):
     P = Poisson(N)
     return lambda u: P.solve(-lam * np.exp(u))
+
+
+def em_mixture(copies: int, seed: int = 0, count: int = 100_000,
+               alpha=(0.3, 0.3, 0.4), sigma=(1.0, 1.0, 1.0)):
+    """The mixture-means EM map (Sec. 5.3): count samples from the poorly
+    separated mixture with means (0, 0.5, 1) (aa_synth.mixture_samples), known
+    proportions alpha and deviations sigma; one EM step replaces each mean by
+    the posterior-weighted sample mean.  The three means are repeated copies
+    times along the vector, as the paper does; every copy stays identical
+    under AA (gamma is global), so G evaluates the first copy and repeats it.
+    """
+    import aa_synth
+    X = aa_synth.mixture_samples(seed, count)
+    al = np.asarray(alpha, dtype=np.float64)
+    sg = np.asarray(sigma, dtype=np.float64)
+
+    def step(mu):
+        dens = al * np.exp(-(X[:, None] - mu[None, :]) ** 2 / (2.0 * sg ** 2)) / (np.sqrt(2.0 * np.pi) * sg)
+        post = dens / dens.sum(axis=1, keepdims=True)
+        return (post * X[:, None]).sum(axis=0) / post.sum(axis=0)
+
+    def G(u):
+        return np.tile(step(np.asarray(u[:3])), copies)
+
+    return G, step

@@ -56,3 +56,36 @@ def test_bratu_67(ora, orth):
     r = ora_solve(ora, G, 30, orth, dcgs2_scaled=scaled)
     assert r["status"] == ora.OK and it_g < 30, (it_g, r["iters"])
     assert abs(it_g - r["iters"]) <= 1, (it_g, r["iters"])
+
+
+@pytest.mark.parametrize("orth", ["mgs", "icwy", "cgs2", "dcgs2"])
+def test_em_mixture(ora, orth):
+    """EM for the mixture means (Sec. 5.3) at the paper's local vector size
+    1.5e6 (500,000 copies of the three means), AA(3), tol 1e-8."""
+    import paper_2110_09667_gb300 as aa
+    from paper_problems import em_mixture
+    copies = 500_000
+    n = 3 * copies
+    G, step = em_mixture(copies, 0)
+    mu0 = np.tile([-1.0, 0.0, 1.0], copies)
+    A = aa.Anderson(n, 3, orth)
+    x = mu0.copy()
+    xd = torch.from_numpy(x).cuda()
+    xn = torch.empty_like(xd)
+    it_g = None
+    for i in range(200):
+        g = torch.from_numpy(G(x)).cuda()
+        A.step(xd, g, xn)
+        xnew = xn.cpu().numpy()
+        if np.linalg.norm(xnew - x) < 1e-8:
+            it_g, x = i + 1, xnew
+            break
+        x = xnew
+        xd, xn = xn, xd
+    O = ora.Oracle(n, 3, orth)
+    r = O.solve({"kind": "callback", "fn": G}, mu0, max_iters=200, tol=1e-8, scale=1.0, stop_kind=1)
+    assert it_g is not None and r["status"] == ora.OK
+    assert abs(it_g - r["iters"]) <= 1, (it_g, r["iters"])
+    assert np.max(np.abs(x[:3] - r["x"][:3])) < 1e-7
+    # every copy holds the same means
+    assert np.max(np.abs(x.reshape(-1, 3) - x[:3])) < 1e-12

@@ -51,3 +51,51 @@ def test_heat_term2_cgs2_converges(ora):
     r = solve(ora, G, 10, "cgs2")
     assert r["status"] == ora.OK and r["iters"] <= 45, r["iters"]
     assert np.max(np.abs(r["x"] - ue)) < 1e-5
+
+
+# EM for the means of a three-component normal mixture (Sec. 5.3): AA(3),
+# tolerance 1e-8 on ||x_{i+1} - x_i||_2, 21 iterations for every variant in
+# the paper (one sample draw, initial means not stated; here mu_0 = (-1, 0, 1)).
+EM_MU0 = (-1.0, 0.0, 1.0)
+
+
+def em_solve(ora, G, copies, orth, max_iters=200):
+    O = ora.Oracle(3 * copies, 3, orth)
+    return O.solve({"kind": "callback", "fn": G}, np.tile(EM_MU0, copies), max_iters=max_iters,
+                   tol=1e-8, scale=1.0, stop_kind=1)
+
+
+def test_em_same_count_for_every_variant_near_21(ora):
+    from paper_problems import em_mixture
+    med = []
+    for seed in range(5):
+        G, step = em_mixture(1000, seed)
+        its = []
+        for orth in ["mgs", "icwy", "cgs2", "dcgs2"]:
+            r = em_solve(ora, G, 1000, orth)
+            assert r["status"] == ora.OK, (seed, orth)
+            its.append(r["iters"])
+            mu = r["x"][:3]
+            # a fixed point of the EM map, and the copies stayed identical
+            assert np.max(np.abs(step(mu) - mu)) < 1e-8
+            assert np.max(np.abs(r["x"].reshape(-1, 3) - mu)) == 0.0
+        # the same count up to one (rounding at the stop threshold)
+        assert max(its) - min(its) <= 1, (seed, its)
+        med.append(min(its))
+    assert abs(np.median(med) - 21) <= 4, med
+
+
+def test_em_aa_beats_plain_em(ora):
+    from paper_problems import em_mixture
+    G, step = em_mixture(1, 0)
+    r = em_solve(ora, G, 1, "mgs")
+    mu, k = np.array(EM_MU0), 0
+    while k < 5000:
+        mn = step(mu)
+        k += 1
+        if np.linalg.norm(mn - mu) < 1e-8:
+            break
+        mu = mn
+    # the poorly separated mixture makes plain EM crawl
+    assert k > 20 * r["iters"], (k, r["iters"])
+    assert np.max(np.abs(mn - r["x"][:3])) < 1e-6
