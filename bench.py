@@ -53,9 +53,17 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-wall", action="store_true")
     p.add_argument("--cpu-iters", type=int, default=12)
-    p.add_argument("--workload", default="jacobi3d", choices=["jacobi3d", "bratu-batch"],
+    p.add_argument("--workload", default="jacobi3d",
+                   choices=["jacobi3d", "bratu-batch", "bratu-warmstart"],
                    help="jacobi3d: the headline single solve; bratu-batch: 4096 batched Bratu "
-                        "solves in one persistent launch (reported separately)")
+                        "solves in one persistent launch; bratu-warmstart: the learned warm "
+                        "start on 256^2 Bratu with source (each reported separately)")
+    p.add_argument("--ws-side", type=int, default=256)
+    p.add_argument("--ws-train", type=int, default=20000)
+    p.add_argument("--ws-test", type=int, default=1000)
+    p.add_argument("--ws-epochs", type=int, default=40)
+    p.add_argument("--ws-chunk", type=int, default=2432)
+    p.add_argument("--ws-max-iters", type=int, default=20000)
     p.add_argument("--batch-count", type=int, default=4096)
     p.add_argument("--batch-max-iters", type=int, default=100000)
     return p.parse_args()
@@ -281,7 +289,7 @@ def run_ours(args, ws, rank, local):
             with open(tr_path) as f:
                 tr = json.load(f)
             key = f"{args.orth}_{args.storage}_m{args.m}_{dom}"
-            if key in tr:
+            if key in tr and args.nz == NZ:
                 traffic = tr[key]["bytes_per_launch_full_n"]
         except Exception:
             traffic = None
@@ -539,11 +547,103 @@ def run_batch(args, ws, rank, local):
     }
 
 
+def run_warmstart(args, ws_, rank, local):
+    """Learned warm start on parametric 2D Bratu with source (s x s grid,
+    lambda ~ U(1, 6), 8 x 8 sine modes with N(0, 1) weights): batched AA(10)
+    solves from x0 = 0 give the training targets, the 65 -> 1024 -> 1024 ->
+    s^2 MLP is trained on the GPU with the library's kernels, and held-out
+    instances are solved from x0 = 0 and from the prediction (with the
+    residual gate).  Solves that do not converge within the cap are left out
+    of training and counted."""
+    import numpy as np
+    import torch
+
+    import paper_2110_09667_gb300 as aa
+    from paper_2110_09667_gb300 import warmstart as W
+    torch.cuda.set_device(local)
+    s, m = args.ws_side, 10
+    n = s * s
+    shape = (512, 1)
+    t_all = time.perf_counter()
+
+    def solve_chunks(seeds, x0=None):
+        its, sts, fbs, ms, sol = [], [], [], 0.0, []
+        for c0 in range(0, len(seeds), args.ws_chunk):
+            sd = seeds[c0:c0 + args.ws_chunk]
+            lam, c, src = W.instances(sd, s)
+            xc = None if x0 is None else x0[c0:c0 + len(sd)]
+            U, it, st, t, fb = W.solve_batch(lam, src, s, x0=xc, m=m, max_iters=args.ws_max_iters,
+                                             block=shape[0], ctas_per_sm=shape[1])
+            its.append(it); sts.append(st); fbs.append(fb); ms += t
+            sol.append(U.astype(np.float32))
+        return (np.concatenate(sol), np.concatenate(its), np.concatenate(sts), ms,
+                np.concatenate(fbs))
+
+    # training data
+    tr = np.arange(args.ws_train)
+    U, it_tr, st_tr, ms_tr, _ = solve_chunks(tr)
+    ok = st_tr == 0
+    lam_tr, c_tr, _ = W.instances(tr[ok], 1)
+    X = W.features(lam_tr, c_tr)
+    net = W.MLP(n, seed=1)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    hist = W.train(net, X, U[ok], epochs=args.ws_epochs, batch=128, lr=1e-3)
+    e1.record()
+    torch.cuda.synchronize()
+    train_ms = e0.elapsed_time(e1)
+    del U
+    steps = args.ws_epochs * (int(ok.sum()) // 128)
+    dims = net.dims
+    gemm_flop = 3 * 2 * 128 * sum(dims[i] * dims[i + 1] for i in range(3))  # fwd + 2 bwd GEMMs
+    # held-out
+    te = np.arange(10**6, 10**6 + args.ws_test)
+    lam_te, c_te, _ = W.instances(te, 1)
+    _, it_c, st_c, ms_c, _ = solve_chunks(te)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    x0 = W.predict(net, W.features(lam_te, c_te))
+    inf_ms = (time.perf_counter() - t0) * 1e3
+    _, it_w, st_w, ms_w, fb = solve_chunks(te, x0=x0.astype(np.float64))
+    good = st_c == 0
+    if rank != 0:
+        return None
+
+    def stats(it, st):
+        g = st == 0
+        return {"mean": round(float(it[g].mean()), 1), "p50": int(np.percentile(it[g], 50)),
+                "p99": int(np.percentile(it[g], 99)), "converged": int(g.sum())}
+    warm_total = ms_w + inf_ms
+    return {
+        "metric": f"learned warm start: wall to 1e-8 on {args.ws_test} held-out {s}x{s} Bratu-with-source "
+                  f"solves, x0 = 0 over x0 = MLP (speedup)",
+        "value": round(ms_c / warm_total, 3), "unit": "x", "n_gpus": ws_, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64 solves (fp32 history); bf16 MLP, fp32 accumulate",
+        "data": "synthetic (seeded SplitMix64: lambda ~ U(1,6), c_k ~ N(0,1))",
+        "config": {"workload": f"AA(10) batched Bratu with source {s}x{s}, MLP 65-1024-1024-{n}",
+                   "train_solves": int(args.ws_train), "train_converged": int(ok.sum()),
+                   "test_solves": int(args.ws_test), "epochs": args.ws_epochs, "batch": 128,
+                   "cap": args.ws_max_iters, "launch": {"block": shape[0], "ctas_per_sm": shape[1]}},
+        "cold": dict(stats(it_c, st_c), wall_ms=round(ms_c, 1)),
+        "warm": dict(stats(it_w, st_w), wall_ms=round(warm_total, 1), solve_ms=round(ms_w, 1),
+                     inference_ms=round(inf_ms, 1), fallbacks=int(fb.sum()),
+                     converged_where_cold_did=int((st_w[good] == 0).sum())),
+        "iters_ratio_mean": round(float(it_c[good].mean() / max(1.0, it_w[good].mean())), 3),
+        "train": {"loss_first": hist[0], "loss_last": hist[-1], "ms": round(train_ms, 1),
+                  "steps": steps, "gemm_tflops": round(gemm_flop * steps / (train_ms * 1e-3) / 1e12, 2),
+                  "data_solve_ms": round(ms_tr, 1)},
+        "total_s": round(time.perf_counter() - t_all, 1),
+    }
+
+
 def main():
     args = parse()
     ws, rank, local = dist_setup()
-    if args.workload == "bratu-batch":
-        line = run_batch(args, ws, rank, local)
+    if args.workload in ("bratu-batch", "bratu-warmstart"):
+        run = run_batch if args.workload == "bratu-batch" else run_warmstart
+        line = run(args, ws, rank, local)
         if line is not None:
             print(json.dumps(line), flush=True)
         return

@@ -255,9 +255,10 @@ int64_t aa_batch_rows(const aa_batch *b);
 int aa_batch_set_max_iters(aa_batch *b, int max_iters);
 
 /* e^u for n device doubles computed on the FP32 pipe (the exponential the
- * batched Bratu map uses): range reduction by ln 2 and a degree-13 Taylor
- * polynomial in (hi, lo) float arithmetic, relative error at most about
- * 3 |u| 2^-48 + 2^-45 for |u| < 88.  out_dev may equal u_dev. */
+ * batched Bratu map uses): Tang's table-driven method (reduction by ln2/128,
+ * a 128-entry table of 2^(j/128) and a degree-5 polynomial) in (hi, lo)
+ * float arithmetic, relative error at most about 3 |u| 2^-48 + 2^-45 for
+ * |u| < 86.  out_dev may equal u_dev. */
 int aa_exp_fp32pipe(int64_t n, const double *u_dev, double *out_dev, void *stream);
 
 /* Message for the last error on this thread. */

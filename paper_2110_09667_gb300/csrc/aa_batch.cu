@@ -81,131 +81,200 @@ struct SState {
   unsigned gmask;
 };
 
-__device__ __forceinline__ double warp_sum_d(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// Block reduction of nd values per thread into st.red (fixed order).
-template <int NT>
-__device__ void block_reduce(double *vals, int nd, double *wbuf, SState &st) {
+// Block reduction of nd (hi, lo) float pairs per thread into st.red.  The
+// warp stage combines the pairs on the FP32 pipe (TwoSum butterfly); the
+// per-warp results are folded into FP64 by one thread per value, in warp
+// order (fixed, so the sums are bit-reproducible).
+template <int NT, int ND>
+__device__ void block_reduce_df(const float (&S)[ND], const float (&C)[ND], int nd, float2 *wbuf,
+                                SState &st) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   constexpr int NW = NT / 32;
-  for (int d = 0; d < nd; ++d) {
-    const double v = warp_sum_d(vals[d]);
-    if (lane == 0) wbuf[warp * BNDOT + d] = v;
+#pragma unroll
+  for (int d = 0; d < ND; ++d) {
+    if (d < nd) {
+      float s = S[d], c = C[d];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float s2 = __shfl_xor_sync(0xffffffffu, s, o);
+        const float c2 = __shfl_xor_sync(0xffffffffu, c, o);
+        float hs, ts;
+        aa::two_sum(s, s2, hs, ts);
+        ts = __fadd_rn(ts, __fadd_rn(c, c2));
+        const F2 r = aa::fast_two_sum(hs, ts);
+        s = r.h;
+        c = r.l;
+      }
+      if (lane == 0) wbuf[warp * BNDOT + d] = make_float2(s, c);
+    }
   }
   __syncthreads();
   for (int d = threadIdx.x; d < nd; d += NT) {
     double v = 0.0;
-    for (int w = 0; w < NW; ++w) v += wbuf[w * BNDOT + d];
+    for (int w = 0; w < NW; ++w) {
+      const float2 p = wbuf[w * BNDOT + d];
+      v += aa::f2d(p.x);
+      v += aa::f2d(p.y);
+    }
     st.red[d] = v;
   }
   __syncthreads();
 }
 
+// Software prefetch into L2 of the rows a warp will stream PF row blocks
+// later: lane l < ncols takes FP32 column l (one 128-byte line per 32 rows),
+// lanes 16-23 take up to four FP64 vectors (two lines each).  The batched
+// passes are bound by the latency of their global loads (each thread works
+// through long dependency chains between its loads), and this keeps the next
+// blocks' lines on their way without spending registers.
+constexpr int PF = 2;
+
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+__device__ __forceinline__ void prefetch_rows(int lane, int64_t rb, int64_t n, const float *Q,
+                                              int64_t ldq, int ncols, const double *v0,
+                                              const double *v1, const double *v2,
+                                              const double *v3) {
+  if (rb >= n) return;
+  if (lane < ncols) {
+    prefetch_l2(Q + (int64_t)lane * ldq + rb);
+  } else if (lane >= 16 && lane < 24) {
+    const int w = (lane - 16) >> 1;
+    const int64_t h = (lane & 1) ? 16 : 0;
+    const double *v = w == 0 ? v0 : (w == 1 ? v1 : (w == 2 ? v2 : v3));
+    if (v && rb + h < n) prefetch_l2(v + rb + h);
+  }
+}
+
+// The m x m work below runs on warp 0 with one lane per row or column
+// (m <= BM <= 32): on GB300 a warp-wide FP64 instruction costs the same
+// pipe time whether one lane or all are active, so spreading the O(m^2)
+// loops over the lanes cuts their time by about m.
+
 // Warp 0: Givens parameters of the next QRDelete from R alone, in the scaled
 // two-multiply-add form, plus the rotated R and ICWY's rotated T (as in the
 // single-solve path).
 __device__ void prepare_delete_b(SState &st, int M, int lane) {
-  if (lane == 0) {
-    for (int j = 0; j < M; ++j)
-      for (int l = 0; l < M; ++l) st.Rn[j * BM + l] = (l + 1 < M) ? st.R[j * BM + l + 1] : 0.0;
-    for (int j = 0; j < M; ++j)
-      for (int l = 0; l < M; ++l) {
-        double g = (j == l) ? 1.0 : 0.0;
-        if (j != l && j < M - 1 && l < M - 1) g = (j > l) ? st.T[j * BM + l] : st.T[l * BM + j];
-        st.Tn[j * BM + l] = g;
-      }
-    double tau = st.sig[0];
-    for (int j = 0; j + 1 < M; ++j) {
-      const double av = st.Rn[j * BM + j], bv = st.Rn[(j + 1) * BM + j];
-      const double rho = hypot(av, bv);
-      double c = 1.0, s = 0.0;
-      if (rho != 0.0) {
-        c = av / rho;
-        s = bv / rho;
-      }
-      for (int l = j; l + 1 < M; ++l) {
+  // Rn = R without its first column; Tn = the Gram of the stored columns
+  // 0..M-2 rebuilt from T = I + L (strict lower part mirrored).
+  for (int i = lane; i < BM * BM; i += 32) {
+    const int j = i / BM, l = i % BM;
+    st.Rn[i] = (j < M && l + 1 < M) ? st.R[j * BM + l + 1] : 0.0;
+    double g = (j == l && j < M) ? 1.0 : 0.0;
+    if (j != l && j < M - 1 && l < M - 1) g = (j > l) ? st.T[j * BM + l] : st.T[l * BM + j];
+    st.Tn[i] = g;
+  }
+  __syncwarp();
+  double tau = st.sig[0];  // every lane carries the same value
+  for (int j = 0; j + 1 < M; ++j) {
+    const double av = st.Rn[j * BM + j], bv = st.Rn[(j + 1) * BM + j];
+    const double rho = hypot(av, bv);
+    double c = 1.0, s = 0.0;
+    if (rho != 0.0) {
+      c = av / rho;
+      s = bv / rho;
+    }
+    __syncwarp();
+    {
+      const int l = j + lane;  // rows j, j+1 over columns j..M-2
+      if (l + 1 < M) {
         const double hj = st.Rn[j * BM + l], hj1 = st.Rn[(j + 1) * BM + l];
         st.Rn[j * BM + l] = c * hj + s * hj1;
         st.Rn[(j + 1) * BM + l] = -s * hj + c * hj1;
       }
-      st.Rn[(j + 1) * BM + j] = 0.0;
-      for (int i = 0; i < M; ++i) {
-        const double gj = st.Tn[i * BM + j], gj1 = st.Tn[i * BM + j + 1];
-        st.Tn[i * BM + j] = c * gj + s * gj1;
-        st.Tn[i * BM + j + 1] = -s * gj + c * gj1;
-      }
-      for (int l = 0; l < M; ++l) {
-        const double gj = st.Tn[j * BM + l], gj1 = st.Tn[(j + 1) * BM + l];
-        st.Tn[j * BM + l] = c * gj + s * gj1;
-        st.Tn[(j + 1) * BM + l] = -s * gj + c * gj1;
-      }
-      const double sj1 = st.sig[j + 1];
-      double k1, k2, sout, type;
-      if (fabs(c) >= fabs(s)) {
-        k1 = s * sj1 / (c * tau);
-        k2 = -s * tau / (c * sj1);
-        sout = c * tau;
-        tau = c * sj1;
-        type = 1.0;
-      } else {
-        k1 = c * tau / (s * sj1);
-        k2 = -c * sj1 / (s * tau);
-        sout = s * sj1;
-        tau = -s * tau;
-        type = 0.0;
-      }
+    }
+    if (lane < M) {  // columns j, j+1 of Tn
+      const double gj = st.Tn[lane * BM + j], gj1 = st.Tn[lane * BM + j + 1];
+      st.Tn[lane * BM + j] = c * gj + s * gj1;
+      st.Tn[lane * BM + j + 1] = -s * gj + c * gj1;
+    }
+    __syncwarp();
+    if (lane < M) {  // rows j, j+1 of Tn
+      const double gj = st.Tn[j * BM + lane], gj1 = st.Tn[(j + 1) * BM + lane];
+      st.Tn[j * BM + lane] = c * gj + s * gj1;
+      st.Tn[(j + 1) * BM + lane] = -s * gj + c * gj1;
+    }
+    if (lane == 0) st.Rn[(j + 1) * BM + j] = 0.0;
+    const double sj1 = st.sig[j + 1];
+    double k1, k2, sout, type;
+    if (fabs(c) >= fabs(s)) {
+      k1 = s * sj1 / (c * tau);
+      k2 = -s * tau / (c * sj1);
+      sout = c * tau;
+      tau = c * sj1;
+      type = 1.0;
+    } else {
+      k1 = c * tau / (s * sj1);
+      k2 = -c * sj1 / (s * tau);
+      sout = s * sj1;
+      tau = -s * tau;
+      type = 0.0;
+    }
+    if (lane == 0) {
       st.rot[4 * j] = k1;
       st.rot[4 * j + 1] = k2;
       st.rot[4 * j + 2] = type;
       st.rot[4 * j + 3] = sout;
     }
-    for (int l = 0; l < M; ++l) st.Rn[(M - 1) * BM + l] = 0.0;
-    for (int j = 0; j < M; ++j)
-      for (int l = 0; l < M; ++l) {
-        double v = 0.0;
-        if (j == l && j < M - 1) v = 1.0;
-        else if (l < j && j <= M - 3) v = st.Tn[j * BM + l];
-        st.Tn[j * BM + l] = v;
-      }
-    st.pend = 1;
+    __syncwarp();
   }
+  for (int l = lane; l < M; l += 32) st.Rn[(M - 1) * BM + l] = 0.0;
+  for (int i = lane; i < BM * BM; i += 32) {
+    const int j = i / BM, l = i % BM;
+    double v = 0.0;
+    if (j == l && j < M - 1) v = 1.0;
+    else if (l < j && j <= M - 3) v = st.Tn[i];
+    st.Tn[i] = v;
+  }
+  if (lane == 0) st.pend = 1;
   __syncwarp();
 }
 
 // Warp 0: finish an add (new diagonal, breakdown test, gamma).
 __device__ void finalize_b(SState &st, int m, int k, double rho, double vf, double vscale,
                            int head_new, double bd_tol, int lane) {
-  if (lane == 0) {
-    const bool bd = !(rho > 0.0) || !isfinite(rho) || rho <= bd_tol * sqrt(st.dfn2);
-    if (bd) {
-      for (int j = 0; j < BM; ++j) st.gphys[j] = 0.0;
+  const bool bd = !(rho > 0.0) || !isfinite(rho) || rho <= bd_tol * sqrt(st.dfn2);
+  if (bd) {
+    for (int j = lane; j < BM; j += 32) st.gphys[j] = 0.0;
+    if (lane == 0) {
       st.c = 0;
       st.head = 0;
       st.pend = 0;
       st.restarts++;
-    } else {
-      for (int l = 0; l < m; ++l) st.R[k * BM + l] = 0.0;
-      for (int j = 0; j < k; ++j) st.R[j * BM + k] = st.rcol[j];
+    }
+    __syncwarp();
+  } else {
+    for (int l = lane; l < m; l += 32) st.R[k * BM + l] = 0.0;
+    __syncwarp();
+    for (int j = lane; j < k; j += 32) st.R[j * BM + k] = st.rcol[j];
+    for (int l = lane; l < m; l += 32) st.T[k * BM + l] = (l == k) ? 1.0 : 0.0;
+    if (lane == 0) {
       st.R[k * BM + k] = rho;
       st.sig[k] = 1.0 / (rho * vscale);
-      for (int l = 0; l < m; ++l) st.T[k * BM + l] = (l == k) ? 1.0 : 0.0;
       st.rhs[k] = vf / rho;
-      for (int j = k; j >= 0; --j) {
-        double s = st.rhs[j];
-        for (int l = j + 1; l <= k; ++l) s -= st.R[j * BM + l] * st.gam[l];
-        st.gam[j] = s / st.R[j * BM + j];
-      }
-      for (int j = 0; j < BM; ++j) st.gphys[j] = 0.0;
-      for (int j = 0; j <= k; ++j) st.gphys[(head_new + j) % m] = st.gam[j];
+    }
+    __syncwarp();
+    // R gamma = rhs by columns: lane j holds rhs_j minus the terms of the
+    // unknowns found so far.
+    double sj = (lane <= k) ? st.rhs[lane] : 0.0;
+    for (int l = k; l >= 0; --l) {
+      double gl = 0.0;
+      if (lane == l) gl = sj / st.R[l * BM + l];
+      gl = __shfl_sync(0xffffffffu, gl, l);
+      if (lane < l) sj -= st.R[lane * BM + l] * gl;
+      if (lane == l) st.gam[l] = gl;
+    }
+    for (int j = lane; j < BM; j += 32) st.gphys[j] = 0.0;
+    __syncwarp();
+    if (lane <= k) st.gphys[(head_new + lane) % m] = st.gam[lane];
+    if (lane == 0) {
       st.c = k + 1;
       st.head = head_new;
     }
+    __syncwarp();
   }
-  __syncwarp();
   if (st.c == m && st.pend == 0) prepare_delete_b(st, m, lane);
 }
 
@@ -214,10 +283,12 @@ template <int NT, int MB>
 __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : (NT <= 256 ? 2 : 1)) batch_kernel(BArgs a) {
   constexpr int ND = 3 + 3 * MB;
   __shared__ SState st;
-  __shared__ double wbuf[(NT / 32) * BNDOT];
+  __shared__ float2 wbuf[(NT / 32) * BNDOT];
   __shared__ float cfr[4 * BM], cfc[2 * BM], cfg[2 * BM], cfv[2];
+  __shared__ float2 exptab[aa::EXP_TAB];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int m = a.m;
+  aa::exp_table_init(exptab);
 
   for (;;) {
     if (tid == 0) st.solve = (int)atomicAdd(a.queue, 1u);
@@ -262,18 +333,18 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : (NT <= 256 ? 2 : 1)) batch
         }
         __syncthreads();
       }
-      const int nd = (it == 0) ? 1 : 3 + 3 * k - (k > 0 ? 1 : 0);
       float aS[ND], aC[ND];
 #pragma unroll
       for (int d = 0; d < ND; ++d) aS[d] = aC[d] = 0.f;
       for (int r = tid; r < (int)n; r += NT) {
+        prefetch_rows(lane, r - lane + PF * NT, n, a.Q + off, a.N, (it == 0) ? 0 : c, Xc, FP, GP, src);
         const int j = r / s, i = r - j * s;
         const double x = Xc[r];
         const double w = i > 0 ? Xc[r - 1] : 0.0;
         const double e = i < s - 1 ? Xc[r + 1] : 0.0;
         const double so = j > 0 ? Xc[r - s] : 0.0;
         const double no = j < s - 1 ? Xc[r + s] : 0.0;
-        const double rhs = lam * aa::exp_df(x) + (src ? src[r] : 0.0);
+        const double rhs = lam * aa::exp_df(x, exptab) + (src ? src[r] : 0.0);
         const double g = ((w + e) + (so + no) + h2 * rhs) * 0.25;
         const double f = g - x;
         const F2 f2 = aa::d2f2(f);
@@ -336,13 +407,8 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : (NT <= 256 ? 2 : 1)) batch
             }
           }
       }
-      (void)nd;
-      {
-        double vals[ND];
-#pragma unroll
-        for (int d = 0; d < ND; ++d) vals[d] = aa::f2d(aS[d]) + aa::f2d(aC[d]);
-        block_reduce<NT>(vals, ND, wbuf, st);
-      }
+      // slots: 0 ||f||^2, 1 ||df||^2, 2 df.f, 3+j q_j.f, 3+MB+j q_j.df, 3+2MB+j q_j.q_{k-1}
+      block_reduce_df<NT, ND>(aS, aC, (it == 0) ? 1 : 3 + 2 * MB + (k > 1 ? k - 1 : 0), wbuf, st);
       // ---- warp 0: stop test, R column, T row, projection coefficients
       if (warp == 0) {
         const double fn2 = st.red[0];
@@ -367,29 +433,38 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : (NT <= 256 ? 2 : 1)) batch
           a.res[S.orig].fallback = st.fallback ? 1 : 0;
         }
         __syncwarp();
-        if (!st.done && it > 0 && lane == 0) {
-          st.dfn2 = st.red[1];
+        if (!st.done && it > 0) {
           if (del) {
-            for (int i = 0; i < BM * BM; ++i) {
+            for (int i = lane; i < BM * BM; i += 32) {
               const int jj = i / BM, ll = i % BM;
               st.R[i] = (jj < k && ll < k) ? st.Rn[i] : 0.0;
               st.T[i] = st.Tn[i];
             }
-            for (int jj = 0; jj < k; ++jj) st.sig[jj] = st.rot[4 * jj + 3];
-            st.pend = 0;
+            for (int jj = lane; jj < k; jj += 32) st.sig[jj] = st.rot[4 * jj + 3];
+            if (lane == 0) st.pend = 0;
+            __syncwarp();
           }
-          for (int jj = 0; jj < k; ++jj) st.rhs[jj] = st.sig[jj] * st.red[3 + jj];
-          st.vscale = st.dfn2 > 0.0 ? 1.0 / sqrt(st.dfn2) : 1.0;
+          if (lane == 0) {
+            st.dfn2 = st.red[1];
+            st.vscale = st.dfn2 > 0.0 ? 1.0 / sqrt(st.dfn2) : 1.0;
+          }
+          for (int jj = lane; jj < k; jj += 32) st.rhs[jj] = st.sig[jj] * st.red[3 + jj];
           if (k > 0) {
-            for (int l = 0; l + 1 < k; ++l)
-              st.T[(k - 1) * BM + l] = st.sig[l] * st.sig[k - 1] * st.red[3 + 2 * MB + l];
-            for (int l = k - 1; l < BM; ++l) st.T[(k - 1) * BM + l] = (l == k - 1) ? 1.0 : 0.0;
-            for (int jj = 0; jj < k; ++jj) {
-              double v = st.sig[jj] * st.red[3 + MB + jj];
-              for (int l = 0; l < jj; ++l) v -= st.T[jj * BM + l] * st.rcol[l];
-              st.rcol[jj] = v;
+            // the delayed T row of column k-1, then the R column r = T^{-1} (Q^T df)
+            // by forward substitution with one lane per row
+            for (int l = lane; l < BM; l += 32)
+              st.T[(k - 1) * BM + l] = (l + 1 < k) ? st.sig[l] * st.sig[k - 1] * st.red[3 + 2 * MB + l]
+                                                   : ((l == k - 1) ? 1.0 : 0.0);
+            __syncwarp();
+            double v = (lane < k) ? st.sig[lane] * st.red[3 + MB + lane] : 0.0;
+            for (int l = 0; l + 1 < k; ++l) {
+              const double rl = __shfl_sync(0xffffffffu, v, l);
+              if (lane > l && lane < k) v -= st.T[lane * BM + l] * rl;
             }
-            for (int jj = 0; jj < k; ++jj) st.coef[jj] = st.sig[jj] * st.rcol[jj];
+            if (lane < k) {
+              st.rcol[lane] = v;
+              st.coef[lane] = st.sig[lane] * v;
+            }
           }
         }
         __syncwarp();
@@ -420,6 +495,7 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : (NT <= 256 ? 2 : 1)) batch
         __syncthreads();
         float vS[2] = {0.f, 0.f}, vC[2] = {0.f, 0.f};
         for (int64_t r = tid; r < n; r += NT) {
+          prefetch_rows(lane, r - lane + PF * NT, n, a.Q + off, a.N, k, DF, FP, nullptr, nullptr);
           F2 acc = aa::d2f2(DF[r]);
 #pragma unroll
           for (int jj = 0; jj < MB; ++jj)
@@ -433,8 +509,7 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : (NT <= 256 ? 2 : 1)) batch
           aa::prod_ff(acc, aa::d2f2(FP[r]), p, q);
           aa::acc_add(vS[1], vC[1], p, q);
         }
-        double vals[2] = {aa::f2d(vS[0]) + aa::f2d(vC[0]), aa::f2d(vS[1]) + aa::f2d(vC[1])};
-        block_reduce<NT>(vals, 2, wbuf, st);
+        block_reduce_df<NT, 2>(vS, vC, 2, wbuf, st);
         if (warp == 0)
           finalize_b(st, m, k, sqrt(st.red[0]), st.red[1], st.vscale, head_new, a.breakdown_tol,
                      lane);
@@ -456,6 +531,7 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : (NT <= 256 ? 2 : 1)) batch
       __syncthreads();
       const unsigned gmask = st.gmask;
       for (int64_t r = tid; r < n; r += NT) {
+        prefetch_rows(lane, r - lane + PF * NT, n, a.DG + off, a.N, ng, GP, nullptr, nullptr, nullptr);
         if (ng == 0) {
           Xn[r] = GP[r];
           continue;
@@ -755,9 +831,12 @@ extern "C" int aa_batch_set_max_iters(aa_batch *b, int max_iters) {
 
 namespace {
 __global__ void exp_kernel(int64_t n, const double *__restrict__ u, double *__restrict__ out) {
+  __shared__ float2 tab[aa::EXP_TAB];
+  aa::exp_table_init(tab);
+  __syncthreads();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
-    out[i] = aa::exp_df(u[i]);
+    out[i] = aa::exp_df(u[i], tab);
 }
 }  // namespace
 

@@ -146,48 +146,65 @@ __device__ __forceinline__ F2 df_mad(F2 c, F2 a, F2 b) {
   return fast_two_sum(s, t);
 }
 
-// e^u for a double u on the FP32 pipe.  The split of u and the roundings in
-// the reduced argument's low part carry an absolute error of up to about
-// 3 |u| 2^-48, which becomes a relative error of e^u; the polynomial and the
-// final scaling add a few 2^-48: relative error <= 3 |u| 2^-48 + 2^-45.
-// Range reduction u = k ln2 + r with |r| <= ln2/2, ln2 = L1 + L2 + L3 (L1
-// has a short significand, so k L1 is exact for |k| < 128); then
-// e^r = sum_{j=0}^{13} r^j / j! by Horner's rule in (hi, lo) arithmetic
-// (truncation error below 0.35^14/14! < 2^-52); finally the exact scaling by
-// 2^k.  Returns +inf above the float range, 0 below it.
-__device__ __forceinline__ double exp_df(double u) {
-  // 1/j!, j = 0..13, as (hi, lo) float pairs (hi = 1/j! rounded to float,
-  // lo = the rounded remainder)
-  const float C[14][2] = {{1.0f, 0.0f},
-                          {1.0f, 0.0f},
-                          {0.5f, 0.0f},
-                          {0.1666666716337204f, -4.967053879312289e-09f},
-                          {0.0416666679084301f, -1.2417634698280722e-09f},
-                          {0.008333333767950535f, -4.34617203337595e-10f},
-                          {0.0013888889225199819f, -3.3631094437103215e-11f},
-                          {0.00019841270113829523f, -2.725596874933456e-12f},
-                          {2.4801587642286904e-05f, -3.40699609366682e-13f},
-                          {2.7557318844628753e-06f, 3.793571224297229e-14f},
-                          {2.755731998149713e-07f, -7.575112209051195e-15f},
-                          {2.5052107943679403e-08f, 4.4176230446483665e-16f},
-                          {2.0876755879584152e-09f, 1.1082839147459852e-16f},
-                          {1.6059044372074283e-10f, -5.352526511562726e-18f}};
-  const float L1 = 0x1.62e4p-1f, L2 = 0x1.7f7d1cp-20f, L3 = 0x1.ef357ap-45f;
+// e^u for a double u on the FP32 pipe, table-driven (Tang's method:
+// P. T. P. Tang, "Table-driven implementation of the exponential function
+// in IEEE floating-point arithmetic", ACM TOMS 15(2), 1989).
+//   u = (128 q + j) ln2/128 + r,  |r| <= ln2/256,
+//   e^u = 2^q * 2^(j/128) * e^r,
+// with ln2/128 = L1 + L2 + L3 (L1 has 10 significant bits, so k L1 is exact
+// for |k| < 2^14; L2, L3 are the next two float roundings), the table
+// 2^(j/128) held as (hi, lo) float pairs, and
+//   e^r = 1 + r + r^2/2 + r^3 (1/6 + r/24 + r^2/120),
+// whose truncation error is below r^6/720 < 2^-59 and whose last group
+// (below 2^-27) is evaluated in plain FP32.  Error: the split of u and the
+// roundings in the reduced argument's low part carry an absolute error of up
+// to about 3 |u| 2^-48, which becomes a relative error of e^u; the table and
+// the (hi, lo) products add a few 2^-48: relative error <= 3 |u| 2^-48 +
+// 2^-45.  Returns +inf above e^88.7 and 0 below e^-86.6.
+
+constexpr int EXP_TAB = 128;
+
+// Fills the table tab[j] = 2^(j/128) (one FP64 exp2 per entry, split
+// exactly into two floats); call from every thread of the block, then
+// synchronise before the first exp_df.
+__device__ __forceinline__ void exp_table_init(float2 *tab) {
+  for (int j = threadIdx.x; j < EXP_TAB; j += blockDim.x) {
+    const F2 t = d2f2(exp2((double)j / (double)EXP_TAB));
+    tab[j] = make_float2(t.h, t.l);
+  }
+}
+
+__device__ __forceinline__ double exp_df(double u, const float2 *tab) {
+  const float L1 = 0x1.628p-8f, L2 = 0x1.90bfbep-18f, L3 = 0x1.1cf79ap-43f;
+  const float INV = 0x1.715476p+7f;  // 128 / ln2 rounded to float
   const F2 x = d2f2(u);
-  const float kf = rintf(__fmul_rn(x.h, 1.44269502f));
-  if (kf > 127.f) return __longlong_as_double(0x7ff0000000000000LL);
-  if (kf < -125.f) return 0.0;
+  const float kf = rintf(__fmul_rn(x.h, INV));
+  if (kf > 16383.f) return __longlong_as_double(0x7ff0000000000000LL);
+  if (kf < -16000.f) return 0.0;
+  const int k = (int)kf;
   const float r0 = __fmaf_rn(-kf, L1, x.h);  // exact
   const float p = __fmul_rn(kf, L2), pe = __fmaf_rn(kf, L2, -p);
   float s, t;
   two_sum(r0, -p, s, t);
   const float low = __fadd_rn(__fsub_rn(t, pe), __fsub_rn(x.l, __fmul_rn(kf, L3)));
   const F2 r = fast_two_sum(s, low);
-  F2 P{C[13][0], C[13][1]};
-#pragma unroll
-  for (int j = 12; j >= 0; --j) P = df_mad(P, r, F2{C[j][0], C[j][1]});
-  const float sc = __int_as_float(((int)kf + 127) << 23);
-  return f2d(__fmul_rn(P.h, sc)) + f2d(__fmul_rn(P.l, sc));
+  // r^3 (1/6 + r/24 + r^2/120) in FP32
+  const float c3 = __fmul_rn(__fmul_rn(r.h, __fmul_rn(r.h, r.h)),
+                             __fmaf_rn(r.h, __fmaf_rn(r.h, 1.f / 120.f, 1.f / 24.f), 1.f / 6.f));
+  float q2, q2e;
+  prod_ff(r, r, q2, q2e);
+  F2 S = df_add(r, F2{__fmul_rn(0.5f, q2), __fmul_rn(0.5f, q2e)});  // r + r^2/2
+  S = fast_two_sum(S.h, __fadd_rn(S.l, c3));
+  F2 E = fast_two_sum(1.f, S.h);  // |S| < 2^-8
+  E = fast_two_sum(E.h, __fadd_rn(E.l, S.l));
+  const float2 T = tab[k & (EXP_TAB - 1)];
+  float ph, pl;
+  prod_ff(F2{T.x, T.y}, E, ph, pl);
+  const F2 P = fast_two_sum(ph, pl);
+  // P is in [0.99, 2): join it in FP64, then scale by 2^q through the
+  // exponent field (exact; the result is a normal double for every q here)
+  const double d = f2d(P.h) + f2d(P.l);
+  return __hiloint2double(__double2hiint(d) + ((k >> 7) << 20), __double2loint(d));
 }
 
 }  // namespace aa

@@ -8,6 +8,8 @@ rounded at slightly different points: 1e-4 relative).  Converged solves must
 satisfy the stop rule when checked with the oracle's FP64 map, in an
 iteration count within 10 % of the oracle's.
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -104,10 +106,22 @@ def test_exp_fp32pipe_accuracy(aa):
     3 |u| 2^-48 absolutely, i.e. relatively in e^u; the polynomial and the
     scaling add a few 2^-48: bound 3 |u| 2^-48 + 2^-45."""
     u = torch.linspace(-20.0, 20.0, 200001, dtype=torch.float64, device="cuda")
-    u = torch.cat([u, torch.tensor([0.0, 1e-30, -1e-30, 0.6931471805599453, 3.0], dtype=torch.float64,
-                                   device="cuda")])
+    # both sides of every table boundary (multiples of ln2/128 and the odd
+    # multiples of ln2/256 where the rounding of u 128/ln2 changes)
+    kk = torch.arange(-128 * 120, 128 * 120, dtype=torch.float64, device="cuda")
+    step = math.log(2.0) / 256.0
+    edges = torch.cat([kk * step * (1 + 1e-12), kk * step * (1 - 1e-12)])
+    wide = torch.linspace(-86.0, 86.0, 100001, dtype=torch.float64, device="cuda")
+    u = torch.cat([u, edges, wide,
+                   torch.tensor([0.0, 1e-30, -1e-30, 0.6931471805599453, 3.0], dtype=torch.float64,
+                                device="cuda")])
     got = aa.exp_fp32pipe(u)
     ref = torch.exp(u)
     rel = (got - ref).abs() / ref
     bound = (3.0 * u.abs() + 8.0) * 2.0 ** -48
     assert bool((rel <= bound).all()), (rel / bound).max().item()
+    sp = torch.tensor([float("nan"), float("inf"), -float("inf"), 100.0, -100.0], dtype=torch.float64,
+                      device="cuda")
+    got = aa.exp_fp32pipe(sp).cpu().tolist()
+    assert math.isnan(got[0]) and got[1] == math.inf and got[2] == 0.0
+    assert got[3] == math.inf and got[4] == 0.0
