@@ -524,8 +524,13 @@ def run_batch(args, ws, rank, local):
     ms = B.solve(*shape)
     ck = clocks.stop()
     it, rs, st = B.results()
+    t_start, t_end = B.times()
     n = sides.astype(np.float64) ** 2
     row_iters = float((it.astype(np.float64) * n).sum())
+    # completion profile: the bulk (99 % of the solves done) against the tail
+    t99 = float(np.percentile(t_end, 99))
+    bulk = t_end <= t99
+    bulk_rate = float((it[bulk].astype(np.float64) * n[bulk]).sum()) / (t99 * 1e-3)
     bytes_per_row_iter = 240.0  # FP32 Q/dG, m = 10, recycle: pass A 128 + projection 56 + update 56
     if rank != 0:
         return None
@@ -540,6 +545,9 @@ def run_batch(args, ws, rank, local):
         "iters_max": int(it.max()), "converged": int((st == 0).sum()), "count": int(len(st)),
         "sum_n": int(n.sum()), "row_iterations": row_iters,
         "hbm_gbs_algorithmic": round(row_iters * bytes_per_row_iter / (ms_max * 1e-3) / 1e9, 1),
+        "completion_ms": {"p50": round(float(np.percentile(t_end, 50)), 1), "p99": round(t99, 1),
+                          "max": round(float(t_end.max()), 1)},
+        "bulk_hbm_gbs_algorithmic": round(bulk_rate * bytes_per_row_iter / 1e9, 1),
         "launch": {"block": shape[0], "ctas_per_sm": shape[1], "graph": True,
                    "autotune_ms": {f"{b}x{c}": round(t, 1) for (b, c), t in tuned.items()}},
         "dtype": "f64 (fp32 history storage)", "data": "synthetic (seeded SplitMix64)",

@@ -247,6 +247,11 @@ int aa_batch_results(aa_batch *b, int32_t *iters, double *resid, int32_t *status
 /* Per-solve flag (input order): 1 if the x_0 given by aa_batch_set_x0 was
  * rejected by the residual test and the solve restarted from x_0 = 0. */
 int aa_batch_fallbacks(aa_batch *b, int32_t *fallback);
+/* Per-solve start and stop times of the last aa_batch_solve (input order),
+ * in ms from the earliest start, read from the device's global timer: the
+ * completion profile of the persistent launch (load balance, tail).  Either
+ * pointer may be NULL, not both.  No counterpart in the paper. */
+int aa_batch_times(aa_batch *b, double *start_ms, double *end_ms);
 /* Solution of solve idx (host, n_idx doubles). */
 int aa_batch_solution(aa_batch *b, int idx, double *x_host);
 /* Total arena rows (sum of n_i rounded up to 64 each). */

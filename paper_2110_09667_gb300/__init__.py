@@ -247,6 +247,7 @@ def _batch_lib():
         L.aa_batch_results.argtypes = [C.c_void_p, C.POINTER(C.c_int32), _dp, C.POINTER(C.c_int32)]
         L.aa_batch_solution.argtypes = [C.c_void_p, C.c_int, _dp]
         L.aa_batch_fallbacks.argtypes = [C.c_void_p, C.POINTER(C.c_int32)]
+        L.aa_batch_times.argtypes = [C.c_void_p, _dp, _dp]
         L.aa_batch_rows.argtypes = [C.c_void_p]
         L.aa_batch_rows.restype = C.c_int64
         L.aa_batch_set_max_iters.argtypes = [C.c_void_p, C.c_int]
@@ -316,6 +317,14 @@ class Batch:
         fb = np.zeros(self.count, dtype=np.int32)
         _check(_batch_lib().aa_batch_fallbacks(self._h, fb.ctypes.data_as(C.POINTER(C.c_int32))))
         return fb
+
+    def times(self):
+        """(start_ms, end_ms) per solve of the last solve() call, from the device timer."""
+        import numpy as np
+        t0 = np.zeros(self.count)
+        t1 = np.zeros(self.count)
+        _check(_batch_lib().aa_batch_times(self._h, t0.ctypes.data_as(_dp), t1.ctypes.data_as(_dp)))
+        return t0, t1
 
     def solution(self, i: int):
         import numpy as np

@@ -51,7 +51,14 @@ struct Result {
   double resid;      // ||f||/||G(0)|| at exit
   int32_t fallback;  // 1 if the given x_0 was replaced by 0
   int32_t pad;
+  uint64_t t0, t1;   // device global timer (ns) when the solve started and stopped
 };
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 struct BArgs {
   const Solve *solves;
@@ -146,6 +153,29 @@ __device__ __forceinline__ void prefetch_rows(int lane, int64_t rb, int64_t n, c
     const double *v = w == 0 ? v0 : (w == 1 ? v1 : (w == 2 ? v2 : v3));
     if (v && rb + h < n) prefetch_l2(v + rb + h);
   }
+}
+
+// Per-thread asynchronous copies (cp.async) of the next row block's
+// streamed operands into a two-stage shared-memory buffer: each thread
+// copies, and later reads, only its own slots, so a per-thread wait on the
+// older copy group is the only synchronisation needed.
+__device__ __forceinline__ void cp_async8(void *sdst, const void *gsrc) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *sdst, const void *gsrc) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Staging buffer bytes: 2 stages x NT threads x (4 doubles + MB floats).
+__host__ __device__ constexpr size_t stage_bytes(int nt, int mb) {
+  return (size_t)2 * nt * (4 * sizeof(double) + mb * sizeof(float));
 }
 
 // The m x m work below runs on warp 0 with one lane per row or column
@@ -286,8 +316,14 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : (NT <= 256 ? 2 : 1)) batch
   __shared__ float2 wbuf[(NT / 32) * BNDOT];
   __shared__ float cfr[4 * BM], cfc[2 * BM], cfg[2 * BM], cfv[2];
   __shared__ float2 exptab[aa::EXP_TAB];
+  extern __shared__ __align__(16) unsigned char dsm[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int m = a.m;
+  // staged operands: sd[stage][vector][thread] (FP64), sq[stage][column][thread] (FP32)
+  double *const sd = (double *)dsm;
+  float *const sq = (float *)(sd + 2 * 4 * NT);
+  auto SD = [&](int sg, int v) -> double & { return sd[(sg * 4 + v) * NT + tid]; };
+  auto SQ = [&](int sg, int jj) -> float & { return sq[(sg * MB + jj) * NT + tid]; };
   aa::exp_table_init(exptab);
 
   for (;;) {
@@ -296,6 +332,7 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : (NT <= 256 ? 2 : 1)) batch
     const int si = st.solve;
     if (si >= a.count) return;
     const Solve S = a.solves[si];
+    if (tid == 0) a.res[S.orig].t0 = global_ns();
     const int s = S.s;
     const int64_t n = (int64_t)s * s, off = S.off;
     const double h = 1.0 / (double)(s + 1), h2 = h * h, lam = S.lambda;
@@ -336,15 +373,33 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : (NT <= 256 ? 2 : 1)) batch
       float aS[ND], aC[ND];
 #pragma unroll
       for (int d = 0; d < ND; ++d) aS[d] = aC[d] = 0.f;
-      for (int r = tid; r < (int)n; r += NT) {
+      auto stageA = [&](int rr, int sg) {
+        if (rr < (int)n) {
+          cp_async8(&SD(sg, 0), Xc + rr);
+          if (src) cp_async8(&SD(sg, 3), src + rr);
+          if (it > 0) {
+            cp_async8(&SD(sg, 1), FP + rr);
+            cp_async8(&SD(sg, 2), GP + rr);
+#pragma unroll
+            for (int jj = 0; jj < MB; ++jj)
+              if (jj < c) cp_async4(&SQ(sg, jj), a.Q + (int64_t)jj * a.N + off + rr);
+          }
+        }
+        cp_async_commit();
+      };
+      stageA(tid, 0);
+      int sgA = 0;
+      for (int r = tid; r < (int)n; r += NT, sgA ^= 1) {
+        stageA(r + NT, sgA ^ 1);
         prefetch_rows(lane, r - lane + PF * NT, n, a.Q + off, a.N, (it == 0) ? 0 : c, Xc, FP, GP, src);
+        cp_async_wait<1>();
         const int j = r / s, i = r - j * s;
-        const double x = Xc[r];
+        const double x = SD(sgA, 0);
         const double w = i > 0 ? Xc[r - 1] : 0.0;
         const double e = i < s - 1 ? Xc[r + 1] : 0.0;
         const double so = j > 0 ? Xc[r - s] : 0.0;
         const double no = j < s - 1 ? Xc[r + s] : 0.0;
-        const double rhs = lam * aa::exp_df(x, exptab) + (src ? src[r] : 0.0);
+        const double rhs = lam * aa::exp_df(x, exptab) + (src ? SD(sgA, 3) : 0.0);
         const double g = ((w + e) + (so + no) + h2 * rhs) * 0.25;
         const double f = g - x;
         const F2 f2 = aa::d2f2(f);
@@ -356,7 +411,7 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : (NT <= 256 ? 2 : 1)) batch
           GP[r] = g;
           continue;
         }
-        const double df = f - FP[r], dg = g - GP[r];
+        const double df = f - SD(sgA, 1), dg = g - SD(sgA, 2);
         a.DG[(int64_t)dg_slot * a.N + off + r] = aa::d2f_rn(dg);
         DF[r] = df;
         FP[r] = f;
@@ -370,7 +425,7 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : (NT <= 256 ? 2 : 1)) batch
         float qv[MB];
 #pragma unroll
         for (int jj = 0; jj < MB; ++jj)
-          if (jj < c) qv[jj] = a.Q[(int64_t)jj * a.N + off + r];
+          if (jj < c) qv[jj] = SQ(sgA, jj);
         if (del) {
           F2 wv{qv[0], 0.f};
 #pragma unroll
@@ -408,6 +463,7 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : (NT <= 256 ? 2 : 1)) batch
           }
       }
       // slots: 0 ||f||^2, 1 ||df||^2, 2 df.f, 3+j q_j.f, 3+MB+j q_j.df, 3+2MB+j q_j.q_{k-1}
+      cp_async_wait<0>();
       block_reduce_df<NT, ND>(aS, aC, (it == 0) ? 1 : 3 + 2 * MB + (k > 1 ? k - 1 : 0), wbuf, st);
       // ---- warp 0: stop test, R column, T row, projection coefficients
       if (warp == 0) {
@@ -431,6 +487,7 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : (NT <= 256 ? 2 : 1)) batch
           a.res[S.orig].resid = resid;
           a.res[S.orig].status = st.status;
           a.res[S.orig].fallback = st.fallback ? 1 : 0;
+          if (st.done) a.res[S.orig].t1 = global_ns();
         }
         __syncwarp();
         if (!st.done && it > 0) {
@@ -494,21 +551,35 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : (NT <= 256 ? 2 : 1)) batch
         }
         __syncthreads();
         float vS[2] = {0.f, 0.f}, vC[2] = {0.f, 0.f};
-        for (int64_t r = tid; r < n; r += NT) {
+        auto stageP = [&](int64_t rr, int sg) {
+          if (rr < n) {
+            cp_async8(&SD(sg, 0), DF + rr);
+            cp_async8(&SD(sg, 1), FP + rr);
+#pragma unroll
+            for (int jj = 0; jj < MB; ++jj)
+              if (jj < k) cp_async4(&SQ(sg, jj), a.Q + (int64_t)jj * a.N + off + rr);
+          }
+          cp_async_commit();
+        };
+        stageP(tid, 0);
+        int sgP = 0;
+        for (int64_t r = tid; r < n; r += NT, sgP ^= 1) {
+          stageP(r + NT, sgP ^ 1);
           prefetch_rows(lane, r - lane + PF * NT, n, a.Q + off, a.N, k, DF, FP, nullptr, nullptr);
-          F2 acc = aa::d2f2(DF[r]);
+          cp_async_wait<1>();
+          F2 acc = aa::d2f2(SD(sgP, 0));
 #pragma unroll
           for (int jj = 0; jj < MB; ++jj)
-            if (jj < k) acc = aa::df_axpy_f(acc, F2{cfc[2 * jj], cfc[2 * jj + 1]},
-                                            a.Q[(int64_t)jj * a.N + off + r]);
+            if (jj < k) acc = aa::df_axpy_f(acc, F2{cfc[2 * jj], cfc[2 * jj + 1]}, SQ(sgP, jj));
           float p, q;
           aa::prod_ff(acc, F2{cfv[0], cfv[1]}, p, q);
           a.Q[(int64_t)k * a.N + off + r] = __fadd_rn(p, q);
           aa::prod_ff(acc, acc, p, q);
           aa::acc_add(vS[0], vC[0], p, q);
-          aa::prod_ff(acc, aa::d2f2(FP[r]), p, q);
+          aa::prod_ff(acc, aa::d2f2(SD(sgP, 1)), p, q);
           aa::acc_add(vS[1], vC[1], p, q);
         }
+        cp_async_wait<0>();
         block_reduce_df<NT, 2>(vS, vC, 2, wbuf, st);
         if (warp == 0)
           finalize_b(st, m, k, sqrt(st.red[0]), st.red[1], st.vscale, head_new, a.breakdown_tol,
@@ -530,20 +601,33 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : (NT <= 256 ? 2 : 1)) batch
       }
       __syncthreads();
       const unsigned gmask = st.gmask;
-      for (int64_t r = tid; r < n; r += NT) {
+      auto stageU = [&](int64_t rr, int sg) {
+        if (rr < n) {
+          cp_async8(&SD(sg, 0), GP + rr);
+#pragma unroll
+          for (int jj = 0; jj < MB; ++jj)
+            if ((gmask >> jj) & 1u) cp_async4(&SQ(sg, jj), a.DG + (int64_t)jj * a.N + off + rr);
+        }
+        cp_async_commit();
+      };
+      stageU(tid, 0);
+      int sgU = 0;
+      for (int64_t r = tid; r < n; r += NT, sgU ^= 1) {
+        stageU(r + NT, sgU ^ 1);
         prefetch_rows(lane, r - lane + PF * NT, n, a.DG + off, a.N, ng, GP, nullptr, nullptr, nullptr);
+        cp_async_wait<1>();
         if (ng == 0) {
-          Xn[r] = GP[r];
+          Xn[r] = SD(sgU, 0);
           continue;
         }
-        F2 acc = aa::d2f2(GP[r]);
+        F2 acc = aa::d2f2(SD(sgU, 0));
 #pragma unroll
         for (int jj = 0; jj < MB; ++jj)
           if ((gmask >> jj) & 1u)
-            acc = aa::df_axpy_f(acc, F2{cfg[2 * jj], cfg[2 * jj + 1]},
-                                a.DG[(int64_t)jj * a.N + off + r]);
+            acc = aa::df_axpy_f(acc, F2{cfg[2 * jj], cfg[2 * jj + 1]}, SQ(sgU, jj));
         Xn[r] = aa::f22d(acc);
       }
+      cp_async_wait<0>();
       __syncthreads();
       double *tmp = Xc;
       Xc = Xn;
@@ -688,13 +772,46 @@ extern "C" void aa_batch_destroy(aa_batch *b) {
   delete b;
 }
 
+template <int NT, int MB>
+static cudaError_t launch_mb(const BArgs &a, int grid, cudaStream_t s) {
+  batch_kernel<NT, MB><<<grid, NT, stage_bytes(NT, MB), s>>>(a);
+  return cudaGetLastError();
+}
+
 template <int NT>
 static cudaError_t launch_batch(const BArgs &a, int grid, cudaStream_t s) {
-  if (a.m <= 4) batch_kernel<NT, 4><<<grid, NT, 0, s>>>(a);
-  else if (a.m <= 8) batch_kernel<NT, 8><<<grid, NT, 0, s>>>(a);
-  else if (a.m <= 12) batch_kernel<NT, 12><<<grid, NT, 0, s>>>(a);
-  else batch_kernel<NT, 16><<<grid, NT, 0, s>>>(a);
-  return cudaGetLastError();
+  if (a.m <= 4) return launch_mb<NT, 4>(a, grid, s);
+  if (a.m <= 8) return launch_mb<NT, 8>(a, grid, s);
+  if (a.m <= 12) return launch_mb<NT, 12>(a, grid, s);
+  return launch_mb<NT, 16>(a, grid, s);
+}
+
+// The staging buffer is dynamic shared memory (up to 96 KB at 512 threads):
+// raise every instance's limit once, outside any stream capture.
+template <int NT>
+static cudaError_t smem_attr_nt() {
+  cudaError_t e = cudaSuccess;
+  const int mbs[4] = {4, 8, 12, 16};
+  for (int mb : mbs) {
+    const void *f = mb == 4    ? (const void *)batch_kernel<NT, 4>
+                    : mb == 8  ? (const void *)batch_kernel<NT, 8>
+                    : mb == 12 ? (const void *)batch_kernel<NT, 12>
+                               : (const void *)batch_kernel<NT, 16>;
+    const cudaError_t r = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)stage_bytes(NT, mb));
+    if (r != cudaSuccess) e = r;
+  }
+  return e;
+}
+
+static cudaError_t smem_attrs() {
+  static bool done = false;  // per process; the attribute holds for every device context
+  if (done) return cudaSuccess;
+  cudaError_t e = smem_attr_nt<128>();
+  if (e == cudaSuccess) e = smem_attr_nt<256>();
+  if (e == cudaSuccess) e = smem_attr_nt<512>();
+  if (e == cudaSuccess) done = true;
+  return e;
 }
 
 static cudaError_t enqueue(aa_batch *b, int block, int cps, cudaStream_t s) {
@@ -740,6 +857,10 @@ extern "C" int aa_batch_solve(aa_batch *b, int block, int ctas_per_sm, void *str
   if (block != 128 && block != 256 && block != 512) block = 256;
   if (ctas_per_sm < 1 || ctas_per_sm > 4) ctas_per_sm = 1;
   cudaStream_t s = (cudaStream_t)stream;
+  if (smem_attrs() != cudaSuccess) {
+    cudaGetLastError();
+    return AA_ECUDA;
+  }
   // The whole batch is one persistent kernel; it is captured once per
   // (block, ctas_per_sm) into a CUDA graph and replayed.
   if (!b->gexec || b->block != block || b->ctas_per_sm != ctas_per_sm) {
@@ -813,6 +934,21 @@ extern "C" int aa_batch_solution(aa_batch *b, int idx, double *x_host) {
       return AA_OK;
     }
   return AA_EINVAL;
+}
+
+extern "C" int aa_batch_times(aa_batch *b, double *start_ms, double *end_ms) {
+  if (!b || (!start_ms && !end_ms)) return AA_EINVAL;
+  std::vector<Result> r(b->count);
+  if (cudaMemcpy(r.data(), b->dres, sizeof(Result) * b->count, cudaMemcpyDeviceToHost) !=
+      cudaSuccess)
+    return AA_ECUDA;
+  uint64_t t_min = UINT64_MAX;
+  for (const Result &x : r) t_min = std::min(t_min, x.t0);
+  for (int i = 0; i < b->count; ++i) {
+    if (start_ms) start_ms[i] = (double)(r[i].t0 - t_min) * 1e-6;
+    if (end_ms) end_ms[i] = (double)(r[i].t1 - t_min) * 1e-6;
+  }
+  return AA_OK;
 }
 
 extern "C" int64_t aa_batch_rows(const aa_batch *b) { return b ? b->N : 0; }
