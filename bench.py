@@ -58,7 +58,7 @@ def parse():
                    help="jacobi3d: the headline single solve; bratu-batch: 4096 batched Bratu "
                         "solves in one persistent launch; bratu-warmstart: the learned warm "
                         "start on 256^2 Bratu with source (each reported separately)")
-    p.add_argument("--ws-side", type=int, default=256)
+    p.add_argument("--ws-side", type=int, default=128)
     p.add_argument("--ws-train", type=int, default=20000)
     p.add_argument("--ws-test", type=int, default=1000)
     p.add_argument("--ws-epochs", type=int, default=40)

@@ -266,6 +266,49 @@ int aa_batch_set_max_iters(aa_batch *b, int max_iters);
  * |u| < 86.  out_dev may equal u_dev. */
 int aa_exp_fp32pipe(int64_t n, const double *u_dev, double *out_dev, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Learned warm start (no counterpart in the paper): the kernels that train
+ * and run the MLP mapping a parametric problem's parameters to an initial
+ * guess x_0.  All pointers are device pointers, all matrices row-major with
+ * the given leading dimensions (elements); every call is asynchronous on
+ * `stream` and returns AA_EINVAL for bad sizes, null or misaligned pointers
+ * and AA_ECUDA for a launch failure.
+ * ---------------------------------------------------------------------- */
+
+/* C = A B^T on the tensor cores: A [M x K] and B [N x K] BF16 (K, lda, ldb
+ * multiples of 8, A and B 16-byte aligned), FP32 accumulation.  epi bits:
+ * 1 add bias[N] (fp32), 2 GELU, 4 store C as BF16 (else FP32), 8 also store
+ * the pre-GELU value to pre (fp32, leading dimension ldp), 16 add to the
+ * FP32 C already in place (not with 4). */
+int aa_gemm_bf16_nt(int M, int N, int K, const void *A, int lda, const void *B, int ldb, void *C,
+                    int ldc, const float *bias, float *pre, int ldp, int epi, void *stream);
+/* out[c][r] = in[r][c] for a [rows x cols] BF16 matrix. */
+int aa_transpose_bf16(int rows, int cols, const void *in, int ldi, void *out, int ldo,
+                      void *stream);
+/* grad[i] *= GELU'(pre[i]) in place (grad BF16, pre FP32, n elements). */
+int aa_gelu_bwd(int64_t n, const float *pre, void *grad, void *stream);
+/* Mean-squared error of y against t (n FP32 each): dy = 2 (y - t) * scale
+ * (BF16) and the per-block sums of (y - t)^2 in block_loss[nblocks] (FP64,
+ * summed by the caller in block order). */
+int aa_mse(int64_t n, const float *y, const float *t, float scale, void *dy, double *block_loss,
+           int nblocks, void *stream);
+/* out[c] = sum over r of g[r][c] (BF16 in, FP32 out): bias gradients. */
+int aa_colsum_bf16(int rows, int cols, const void *g, int ld, float *out, void *stream);
+/* Adam step (Kingma and Ba 2015) on n FP32 master weights w with moments
+ * m, v and gradient g; refreshes the BF16 copy w_bf16 when not NULL.
+ * step counts from 1 (bias corrections). */
+int aa_adam(int64_t n, float *w, void *w_bf16, const float *g, float *m, float *v, float lr,
+            float beta1, float beta2, float eps, int step, float weight_decay, void *stream);
+/* Momentum SGD on n FP32 master weights: mom = momentum mom + g + wd w,
+ * w -= lr mom; refreshes w_hi = bf16(w) and w_lo = bf16(w - w_hi) when not
+ * NULL (the split copy carries about 16 significant bits). */
+int aa_sgd(int64_t n, float *w, void *w_hi, void *w_lo, const float *g, float *mom, float lr,
+           float momentum, float weight_decay, void *stream);
+/* y = bf16(x) for n values. */
+int aa_f32_to_bf16(int64_t n, const float *x, void *y, void *stream);
+/* hi = bf16(x), lo = bf16(x - hi) for n values. */
+int aa_f32_split_bf16(int64_t n, const float *x, void *hi, void *lo, void *stream);
+
 /* Message for the last error on this thread. */
 const char *aa_last_error(void);
 const char *aa_strerror(int code);

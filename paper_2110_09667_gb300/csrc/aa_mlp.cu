@@ -78,7 +78,8 @@ __device__ __forceinline__ void load_tile(__nv_bfloat16 *s, const __nv_bfloat16 
 }
 
 // epi: bit 0 add bias, bit 1 GELU, bit 2 store bf16 (else fp32), bit 3 also
-// store the pre-activation (fp32) to P.
+// store the pre-activation (fp32) to P, bit 4 add the product to the fp32 C
+// already in place (C += A B^T).
 __global__ void __launch_bounds__(GEMM_THREADS)
     gemm_nt_kernel(int M, int N, int K, const __nv_bfloat16 *__restrict__ A, int lda,
                    const __nv_bfloat16 *__restrict__ B, int ldb, void *C, int ldc,
@@ -148,6 +149,7 @@ __global__ void __launch_bounds__(GEMM_THREADS)
           if (cc >= N) continue;
           float v = acc[i][j][h * 2 + q];
           if (epi & 1) v += bias[cc];
+          if (epi & 16) v += ((const float *)C)[(size_t)row * ldc + cc];
           if (epi & 8) P[(size_t)row * ldp + cc] = v;
           if (epi & 2) v = gelu(v);
           if (epi & 4)
@@ -227,6 +229,34 @@ __global__ void adam_kernel(int64_t n, float *w, __nv_bfloat16 *wb, const float 
   }
 }
 
+// Momentum SGD with FP32 master weights, refreshing a split BF16 copy
+// w ~ hi + lo (both BF16: about 16 significant bits together).
+__global__ void sgd_kernel(int64_t n, float *w, __nv_bfloat16 *hi, __nv_bfloat16 *lo,
+                           const float *__restrict__ g, float *mom, float lr, float mu, float wd) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float mi = mu * mom[i] + g[i] + wd * w[i];
+    mom[i] = mi;
+    const float wi = w[i] - lr * mi;
+    w[i] = wi;
+    if (hi) {
+      const __nv_bfloat16 h = __float2bfloat16_rn(wi);
+      hi[i] = h;
+      if (lo) lo[i] = __float2bfloat16_rn(wi - __bfloat162float(h));
+    }
+  }
+}
+
+__global__ void split_bf16_kernel(int64_t n, const float *__restrict__ x, __nv_bfloat16 *hi,
+                                  __nv_bfloat16 *lo) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(x[i]);
+    hi[i] = h;
+    lo[i] = __float2bfloat16_rn(x[i] - __bfloat162float(h));
+  }
+}
+
 __global__ void f32_to_bf16_kernel(int64_t n, const float *__restrict__ x, __nv_bfloat16 *y) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
@@ -248,6 +278,7 @@ extern "C" int aa_gemm_bf16_nt(int M, int N, int K, const void *A, int lda, cons
   if (M < 1 || N < 1 || K < 1 || !A || !B || !C) return AA_EINVAL;
   if (K % 8 || lda % 8 || ldb % 8 || lda < K || ldb < K || !al16(A) || !al16(B)) return AA_EINVAL;
   if (((epi & 1) && !bias) || ((epi & 8) && !pre)) return AA_EINVAL;
+  if ((epi & 16) && (epi & 4)) return AA_EINVAL;  // accumulation is into fp32 C only
   dim3 grid((N + BNt - 1) / BNt, (M + BMt - 1) / BMt);
   if (grid.y > 65535) return AA_EINVAL;
   gemm_nt_kernel<<<grid, GEMM_THREADS, 0, (cudaStream_t)stream>>>(
@@ -301,5 +332,20 @@ extern "C" int aa_adam(int64_t n, float *w, void *w_bf16, const float *g, float 
 extern "C" int aa_f32_to_bf16(int64_t n, const float *x, void *y, void *stream) {
   if (n < 1 || !x || !y) return AA_EINVAL;
   f32_to_bf16_kernel<<<grid1d(n), 256, 0, (cudaStream_t)stream>>>(n, x, (__nv_bfloat16 *)y);
+  return cudaGetLastError() == cudaSuccess ? AA_OK : AA_ECUDA;
+}
+
+extern "C" int aa_sgd(int64_t n, float *w, void *w_hi, void *w_lo, const float *g, float *mom,
+                      float lr, float momentum, float weight_decay, void *stream) {
+  if (n < 1 || !w || !g || !mom || (w_lo && !w_hi)) return AA_EINVAL;
+  sgd_kernel<<<grid1d(n), 256, 0, (cudaStream_t)stream>>>(
+      n, w, (__nv_bfloat16 *)w_hi, (__nv_bfloat16 *)w_lo, g, mom, lr, momentum, weight_decay);
+  return cudaGetLastError() == cudaSuccess ? AA_OK : AA_ECUDA;
+}
+
+extern "C" int aa_f32_split_bf16(int64_t n, const float *x, void *hi, void *lo, void *stream) {
+  if (n < 1 || !x || !hi || !lo) return AA_EINVAL;
+  split_bf16_kernel<<<grid1d(n), 256, 0, (cudaStream_t)stream>>>(n, x, (__nv_bfloat16 *)hi,
+                                                                 (__nv_bfloat16 *)lo);
   return cudaGetLastError() == cudaSuccess ? AA_OK : AA_ECUDA;
 }

@@ -122,3 +122,50 @@ def test_adam_step(ws):
         ww = ww - 1e-2 * (mm / (1 - 0.9 ** step)) / (np.sqrt(vv / (1 - 0.999 ** step)) + 1e-8)
     assert np.max(np.abs(W.cpu().numpy() - ww)) < 1e-5
     assert np.array_equal(Wb.float().cpu().numpy(), omlp.round_bf16(W.cpu().numpy()).astype(np.float32))
+
+
+def test_gemm_accumulate(ws):
+    """EPI_ACC: C += A B^T onto an FP32 C already in place (the output layer's
+    second, low-order weight product)."""
+    M, N, K = 50, 70, 48
+    A = omlp.round_bf16(aa_synth.normal(21, M * K).reshape(M, K))
+    B = omlp.round_bf16(aa_synth.normal(22, N * K).reshape(N, K))
+    C0 = aa_synth.normal(23, M * N).reshape(M, N).astype(np.float32)
+    C = torch.from_numpy(C0.copy()).cuda()
+    ws.gemm_nt(bf16(A), bf16(B), C, epi=ws.EPI_ACC)
+    ref = C0.astype(np.float64) + A @ B.T
+    bound = 2 * (K + 1) * 2.0 ** -24 * (np.abs(A) @ np.abs(B).T + np.abs(C0))
+    assert np.all(np.abs(C.cpu().numpy() - ref) <= bound)
+
+
+def test_sgd_step_and_split(ws):
+    """Momentum SGD against float64 for two steps; the split copy satisfies
+    hi = bf16(w), lo = bf16(w - hi), so |w - (hi + lo)| <= 2^-16 |w|."""
+    n = 1000
+    w = aa_synth.normal(31, n).astype(np.float32)
+    g = aa_synth.normal(32, n).astype(np.float32)
+    W = torch.from_numpy(w.copy()).cuda()
+    G = torch.from_numpy(g).cuda()
+    mom = torch.zeros(n, device="cuda")
+    hi = torch.empty(n, dtype=torch.bfloat16, device="cuda")
+    lo = torch.empty(n, dtype=torch.bfloat16, device="cuda")
+    L = ws._L()
+    for _ in range(2):
+        assert L.aa_sgd(n, ws._p(W), ws._p(hi), ws._p(lo), ws._p(G), ws._p(mom), 0.05, 0.9, 0.0,
+                        ws._stream()) == 0
+    ww, mm = w.astype(np.float64), np.zeros(n)
+    for _ in range(2):
+        mm = 0.9 * mm + g
+        ww = ww - 0.05 * mm
+    wg = W.cpu().numpy()
+    assert np.max(np.abs(wg - ww)) < 1e-5
+    h = hi.float().cpu().numpy()
+    lw = lo.float().cpu().numpy()
+    assert np.array_equal(h, omlp.round_bf16(wg).astype(np.float32))
+    assert np.array_equal(lw, omlp.round_bf16(wg.astype(np.float64) - h).astype(np.float32))
+    assert np.all(np.abs(wg.astype(np.float64) - h - lw) <= 2.0 ** -16 * np.abs(wg))
+    # the split conversion alone gives the same pair
+    h2 = torch.empty_like(hi)
+    l2 = torch.empty_like(lo)
+    assert L.aa_f32_split_bf16(n, ws._p(W), ws._p(h2), ws._p(l2), ws._stream()) == 0
+    assert torch.equal(h2, hi) and torch.equal(l2, lo)
