@@ -48,6 +48,9 @@ def parse():
     p.add_argument("--storage", default="fp64", choices=["fp64", "fp32", "bf16"])
     p.add_argument("--fp32-dots", action="store_true",
                    help="FP64 storage with dot products on the FP32 pipe (AA_FLAG_FP32_DOTS)")
+    p.add_argument("--df-arith", action="store_true",
+                   help="FP64 storage with (hi, lo) float arithmetic on the FP32/INT pipes "
+                        "(AA_FLAG_DF_ARITH)")
     p.add_argument("--nz", type=int, default=NZ)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
@@ -66,6 +69,11 @@ def parse():
     p.add_argument("--ws-max-iters", type=int, default=20000)
     p.add_argument("--batch-count", type=int, default=4096)
     p.add_argument("--batch-max-iters", type=int, default=100000)
+    p.add_argument("--batch-side", type=int, default=0,
+                   help="every solve on this grid side (default: log-uniform in [32, 256])")
+    p.add_argument("--batch-tol", type=float, default=1e-8)
+    p.add_argument("--batch-shape", default="",
+                   help="launch shape BLOCKxCTAS_PER_SM (skips the autotuner)")
     return p.parse_args()
 
 
@@ -224,7 +232,8 @@ def run_ours(args, ws, rank, local):
     Pp = aa.C.cast(aa.C.pointer(P), aa.C.c_void_p)
     stream = torch.cuda.current_stream()
     sp = stream.cuda_stream
-    flags = aa.FLAG_TIMING | (aa.FLAG_FP32_DOTS if args.fp32_dots else 0)
+    flags = (aa.FLAG_TIMING | (aa.FLAG_FP32_DOTS if args.fp32_dots else 0)
+             | (aa.FLAG_DF_ARITH if args.df_arith else 0))
     A = aa.Anderson(n, args.m, args.orth, args.storage, flags=flags, max_iters=10**6)
     x = torch.zeros(n, dtype=torch.float64, device=dev)
     xn = torch.empty_like(x)
@@ -288,14 +297,15 @@ def run_ours(args, ws, rank, local):
         try:
             with open(tr_path) as f:
                 tr = json.load(f)
-            key = f"{args.orth}_{args.storage}_m{args.m}_{dom}"
+            mode = "_df" if args.df_arith else ("_f32dots" if args.fp32_dots else "")
+            key = f"{args.orth}_{args.storage}{mode}_m{args.m}_{dom}"
             if key in tr and args.nz == NZ:
                 traffic = tr[key]["bytes_per_launch_full_n"]
         except Exception:
             traffic = None
     # Only the exact-FP64 mode runs its row arithmetic on the FP64 pipe; the
     # FP32-history and FP32-dot modes do it on the FP32/INT pipes (HBM-bound form).
-    if args.storage == "fp64" and not args.fp32_dots and fp64_frac > hbm_frac:
+    if args.storage == "fp64" and not (args.fp32_dots or args.df_arith) and fp64_frac > hbm_frac:
         roof = {"bound": "alu", "achieved": round(tflops, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
                 "unit": "TFLOP/s", "frac": round(fp64_frac, 4), "traffic": traffic,
                 "peak_source": "FP64 pipe: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (derived)",
@@ -337,13 +347,15 @@ def run_ours(args, ws, rank, local):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": ("f64" + (" (FP32-pipe dot products)" if args.fp32_dots else ""))
+        "dtype": ("f64" + (" (FP32-pipe dot products)" if args.fp32_dots else "")
+                  + (" storage, (hi, lo) float arithmetic (2^-48 per operation)"
+                     if args.df_arith else ""))
                  if args.storage == "fp64" else f"f64 ({args.storage} history storage)",
         "data": "synthetic (seeded SplitMix64 b ~ U(-1,1), x0 = 0)",
         "config": {"workload": f"AA({args.m}) {args.orth} on 3D 7-pt weighted Jacobi "
                                f"{nx}x{ny}x{nz}, recycle iterations",
                    "n": n, "m": args.m, "orth": args.orth, "storage": args.storage,
-                   "fp32_dots": bool(args.fp32_dots),
+                   "fp32_dots": bool(args.fp32_dots), "df_arith": bool(args.df_arith),
                    "parallelism": f"replicas x{ws}",
                    "l2": "inputs larger than L2 (history %.1f GB per replica)"
                          % (2 * n * args.m * esz / 1e9),
@@ -517,8 +529,13 @@ def run_batch(args, ws, rank, local):
     from paper_2110_09667_gb300 import autotune
     torch.cuda.set_device(local)
     sides, lams = aa_synth.bratu_batch(rank, args.batch_count)
-    shape, tuned = autotune.tune_batch(sides, lams, m=10)
-    B = aa.Batch(sides, lams, m=10, tol=1e-8, max_iters=args.batch_max_iters)
+    if args.batch_side > 0:
+        sides = np.full(args.batch_count, args.batch_side, dtype=np.int64)
+    if args.batch_shape:
+        shape, tuned = tuple(int(v) for v in args.batch_shape.split("x")), {}
+    else:
+        shape, tuned = autotune.tune_batch(sides, lams, m=10)
+    B = aa.Batch(sides, lams, m=10, tol=args.batch_tol, max_iters=args.batch_max_iters)
     clocks = Clocks(local)
     clocks.start()
     ms = B.solve(*shape)
@@ -536,8 +553,9 @@ def run_batch(args, ws, rank, local):
         return None
     ms_max = max_over_ranks(ms)
     return {
-        "metric": f"batched Bratu AA(10) solves/s ({args.batch_count} solves, s ~ log-U[32,256], "
-                  f"tol 1e-8, cap {args.batch_max_iters} iterations)",
+        "metric": f"batched Bratu AA(10) solves/s ({args.batch_count} solves, "
+                  + (f"s = {args.batch_side}" if args.batch_side > 0 else "s ~ log-U[32,256]")
+                  + f", tol {args.batch_tol:g}, cap {args.batch_max_iters} iterations)",
         "value": round(job_rate(args.batch_count, ws, ms_max) / 1.0, 3),
         "unit": "solves/s", "n_gpus": ws, "higher_is_better": True, "scaling": "weak",
         "ms_total": round(ms_max, 1),

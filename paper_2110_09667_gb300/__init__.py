@@ -22,6 +22,7 @@ FLAG_DCGS2_SCALED = 0x1
 FLAG_ICWY_GRAM = 0x2
 FLAG_TIMING = 0x4
 FLAG_FP32_DOTS = 0x8
+FLAG_DF_ARITH = 0x10
 PASS_KINDS = ["init", "A", "proj", "cgs2b", "mgs", "update", "lsq", "mdot"]
 
 AA_OK, AA_NOTCONVERGED = 0, 1

@@ -128,6 +128,9 @@ extern "C" int aa_create(const aa_config *cfg, aa_ctx **out) {
   if (!(cfg->scale > 0)) return fail(AA_EINVAL, "scale must be > 0");
   if ((cfg->flags & AA_FLAG_ICWY_GRAM) && cfg->m > 24)
     return fail(AA_EINVAL, "AA_FLAG_ICWY_GRAM needs m <= 24");
+  if ((cfg->flags & AA_FLAG_DF_ARITH) &&
+      ((cfg->flags & AA_FLAG_FP32_DOTS) || cfg->storage != AA_STORE_FP64))
+    return fail(AA_EINVAL, "AA_FLAG_DF_ARITH needs FP64 storage and no AA_FLAG_FP32_DOTS");
   if (cfg->n > (int64_t)2147483647 * TR) return fail(AA_EINVAL, "n too large");
   aa_ctx *c = (aa_ctx *)calloc(1, sizeof(aa_ctx));
   if (!c) return fail(AA_ENOMEM, "host allocation failed");

@@ -4,7 +4,10 @@
 #include "aa_passes.cuh"
 
 namespace aa {
+cudaError_t launch_pass_f64df(const PassArgs &a, int nsm, int *grid_out, cudaStream_t stream);
+
 cudaError_t launch_pass_f64(const PassArgs &a, int nsm, int *grid_out, cudaStream_t stream) {
+  if (a.flags & 0x10u) return launch_pass_f64df(a, nsm, grid_out, stream);
   if (a.flags & 0x8u) return launch_qm<double, 1>(a, nsm, grid_out, stream);
   return launch_qm<double, 0>(a, nsm, grid_out, stream);
 }

@@ -258,3 +258,66 @@ def test_qradd_fp32_dots(aa, ora, orth):
         tol = 1e-11 if orth != "dcgs2" else 1e-9
         assert np.max(np.abs(Rg - Ro)) <= tol * np.abs(Ro).max(), (j, orth)
         assert np.max(np.abs(Qg - Qo)) <= tol, (j, orth)
+
+
+# ------------------------- FP64 storage, (hi, lo) float arithmetic (MODE 3)
+
+@pytest.mark.parametrize("orth", VARIANTS)
+@pytest.mark.parametrize("m", [5, 10])
+def test_step_parity_df_arith(aa, ora, orth, m):
+    """AA_FLAG_DF_ARITH keeps the FP64 parity contract (iterates to 1e-10 over
+    20 iterations): every n-space operation errs by about 2^-48 relative
+    instead of 2^-53."""
+    nx = ny = 64
+    b = aa_synth.jacobi2d_rhs(0, nx, ny)
+    Gmap = lambda x: ora.g_jacobi2d(nx, ny, 0.01, b, x)
+    out, _ = run_steps(aa, ora, Gmap, nx * ny, m, orth, 21, flags=aa.FLAG_DF_ARITH)
+    for i, (xo, xg, fo, fg) in enumerate(out):
+        assert abs(fg - fo) <= 1e-10 * abs(fo), (i, fo, fg)
+        assert np.linalg.norm(xg - xo) <= 1e-10 * np.linalg.norm(xo), (i, orth, m)
+
+
+@pytest.mark.parametrize("orth", VARIANTS)
+def test_step_parity_df_arith_bratu_ragged(aa, ora, orth):
+    s, lam = 45, 5.0
+    Gmap = lambda u: ora.g_bratu2d(s, lam, None, u)
+    out, _ = run_steps(aa, ora, Gmap, s * s, 4, orth, 20, flags=aa.FLAG_DF_ARITH)
+    for i, (xo, xg, fo, fg) in enumerate(out):
+        assert np.linalg.norm(xg - xo) <= 1e-10 * np.linalg.norm(xo), (i, orth)
+
+
+@pytest.mark.parametrize("orth", VARIANTS)
+@pytest.mark.parametrize("n", [7, 4097])
+def test_qradd_df_arith(aa, ora, orth, n):
+    m = 4
+    V = aa_synth.uniform(61, (m + 4) * n).reshape(m + 4, n)
+    O = ora.Oracle(n, m, orth)
+    G = aa.Anderson(n, m, orth, flags=aa.FLAG_DF_ARITH)
+    for j in range(m + 4):
+        O.qradd(V[j])
+        G.qradd(dev(V[j]))
+        Qo, Ro, _ = O.get_qr()
+        Qg, Rg, _ = G.get_qr()
+        tol = 1e-11 if orth != "dcgs2" else 1e-9
+        assert np.max(np.abs(Rg - Ro)) <= tol * np.abs(Ro).max(), (j, orth)
+        assert np.max(np.abs(Qg - Qo)) <= tol, (j, orth)
+
+
+def test_lsq_df_arith(aa, ora):
+    n, m = 3001, 6
+    V = aa_synth.uniform(62, (m + 1) * n).reshape(m + 1, n)
+    O = ora.Oracle(n, m, "icwy")
+    G = aa.Anderson(n, m, "icwy", flags=aa.FLAG_DF_ARITH)
+    for j in range(m):
+        O.qradd(V[j])
+        G.qradd(dev(V[j]))
+    go = O.lsq(V[m])
+    gg = G.lsq(dev(V[m]))
+    assert np.max(np.abs(gg - go)) <= 1e-11 * np.abs(go).max()
+
+
+def test_df_arith_rejects_other_modes(aa):
+    with pytest.raises(aa.AAError):
+        aa.Anderson(100, 3, "icwy", "fp32", flags=aa.FLAG_DF_ARITH)
+    with pytest.raises(aa.AAError):
+        aa.Anderson(100, 3, "icwy", flags=aa.FLAG_DF_ARITH | aa.FLAG_FP32_DOTS)
