@@ -64,12 +64,14 @@ typedef enum { AA_STORE_FP64 = 0, AA_STORE_FP32 = 1, AA_STORE_BF16 = 2 } aa_stor
                                       splits of the FP64 operands (error <= 2^-45 sum|a_i b_i|
                                       per tile), accumulated in FP64 across tiles; updates of
                                       Q, v and x stay FP64 */
-#define AA_FLAG_DF_ARITH 0x10u     /* FP64 storage: every n-space operation (differences aside)
-                                      on the FP32/INT pipes in (hi, lo) float arithmetic,
-                                      about 2^-48 relative per operation instead of 2^-53;
-                                      Q, dG, x stay FP64 in memory and R, T, gamma stay FP64.
-                                      Not with AA_FLAG_FP32_DOTS or FP32/BF16 storage
-                                      (AA_EINVAL).  No counterpart in the paper. */
+#define AA_FLAG_DF_ARITH 0x10u     /* FP64 storage: the first pass of each QR update (QRDelete
+                                      rotation, first block of dot products) on the FP32/INT
+                                      pipes in (hi, lo) float arithmetic, about 2^-48 relative
+                                      per operation instead of 2^-53; the differences f, df, dg,
+                                      the projection and the update stay FP64, and so do Q, dG,
+                                      x in memory and R, T, gamma.  Not with AA_FLAG_FP32_DOTS
+                                      or FP32/BF16 storage (AA_EINVAL).  No counterpart in the
+                                      paper. */
 
 typedef struct aa_config {
   int64_t n;          /* vector length, >= 1 */

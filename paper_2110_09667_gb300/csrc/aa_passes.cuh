@@ -406,14 +406,14 @@ __device__ __forceinline__ void row_program_df(const PassArgs &a, Stage st, int 
   }
 }
 
-// Row programs for FP64 history with the n-space arithmetic in (hi, lo)
-// float arithmetic on the FP32/INT pipes (AA_FLAG_DF_ARITH).  Stored
-// doubles are split exactly-to-2^-48 into float pairs (integer operations),
-// combined with the multiply-adds of aa_df.cuh and joined back into doubles
-// with one FP64 add; the residual differences f = g - x, df, dg stay exact
-// FP64 adds.  Returns the stage columns it left in shared memory as
-// (hi, lo) pairs (bit c of cv[c >> 6]); the kernel splits the remaining
-// dot-product columns itself.
+// Row program of the first pass (K_A) for FP64 history with the rotation and
+// the dot-product operands in (hi, lo) float arithmetic on the FP32/INT pipes
+// (AA_FLAG_DF_ARITH; the other passes stay on row_program).  Stored doubles
+// are split into float pairs (integer operations, 2^-48 relative), rotated
+// with the multiply-adds of aa_df.cuh and joined back into doubles with one
+// FP64 add; the residual differences f = g - x, df, dg stay exact FP64 adds.
+// Returns the stage columns it left in shared memory as (hi, lo) pairs
+// (bit c of cv[c >> 6]); the kernel splits the remaining dot columns itself.
 __device__ __forceinline__ F2 cfpair(const float *cf, int i) { return F2{cf[i], cf[i + 1]}; }
 
 __device__ __forceinline__ void row_program_dd(const PassArgs &a, Stage st, int t, int r,
@@ -421,128 +421,47 @@ __device__ __forceinline__ void row_program_dd(const PassArgs &a, Stage st, int 
   const int64_t row = (int64_t)t * TR + r;
   auto mark = [&](int c) { cv[c >> 6] |= 1ull << (c & 63); };
   cv[0] = cv[1] = 0ull;
-  switch (a.kind) {
-    case K_INIT: {
-      const double x = st.d(0)[r], g = st.d(1)[r];
-      const double f = g - x;
-      a.out_f[row] = f;
-      a.out_g[row] = g;
-      a.out_x[row] = g;
-      st.put(0, r, d2f2(f));
-      mark(0);
-      break;
-    }
-    case K_A: {
-      double df;
-      if (a.step_mode) {
-        const double x = st.d(0)[r], g = st.d(1)[r], gp = st.d(2)[r], fp = st.d(3)[r];
-        const double f = g - x;
-        df = f - fp;
-        const double dg = g - gp;
-        ((double *)a.out_dg)[row] = dg;
-        a.out_f[row] = f;
-        a.out_g[row] = g;
-        st.put(0, r, d2f2(f));
-        st.put(1, r, d2f2(df));
-        mark(0);
-        mark(1);
+  if (a.kind != K_A) return;
+  double df;
+  if (a.step_mode) {
+    const double x = st.d(0)[r], g = st.d(1)[r], gp = st.d(2)[r], fp = st.d(3)[r];
+    const double f = g - x;
+    df = f - fp;
+    const double dg = g - gp;
+    ((double *)a.out_dg)[row] = dg;
+    a.out_f[row] = f;
+    a.out_g[row] = g;
+    st.put(0, r, d2f2(f));
+    st.put(1, r, d2f2(df));
+    mark(0);
+    mark(1);
+  } else {
+    df = st.d(0)[r];
+    st.put(0, r, d2f2(df));
+    mark(0);
+  }
+  a.out_df[row] = df;
+  if (a.k == 0) ((double *)a.out_q[0])[row] = df;
+  if (a.del) {
+    // the scaled Givens rotations of row_program, as (hi, lo) multiply-adds
+    const int qb = a.qbase;
+    F2 w = d2f2(st.d(qb)[r]);
+    for (int j = 0; j < a.m - 1; ++j) {
+      const F2 u = d2f2(st.d(qb + j + 1)[r]);
+      const F2 k1 = cfpair(cf, CF_ROT + 4 * j), k2 = cfpair(cf, CF_ROT + 4 * j + 2);
+      F2 out, wn;
+      if (__double_as_longlong(co[CO_ROT + 4 * j + 2]) != 0) {
+        out = df_mad(k1, u, w);  // w + k1 u
+        wn = df_mad(k2, w, u);   // u + k2 w
       } else {
-        df = st.d(0)[r];
-        st.put(0, r, d2f2(df));
-        mark(0);
+        out = df_mad(k1, w, u);  // u + k1 w
+        wn = df_mad(k2, u, w);   // w + k2 u
       }
-      a.out_df[row] = df;
-      if (a.k == 0) ((double *)a.out_q[0])[row] = df;
-      if (a.del) {
-        // the scaled Givens rotations of row_program, as (hi, lo) multiply-adds
-        const int qb = a.qbase;
-        F2 w = d2f2(st.d(qb)[r]);
-        for (int j = 0; j < a.m - 1; ++j) {
-          const F2 u = d2f2(st.d(qb + j + 1)[r]);
-          const F2 k1 = cfpair(cf, CF_ROT + 4 * j), k2 = cfpair(cf, CF_ROT + 4 * j + 2);
-          F2 out, wn;
-          if (__double_as_longlong(co[CO_ROT + 4 * j + 2]) != 0) {
-            out = df_mad(k1, u, w);  // w + k1 u
-            wn = df_mad(k2, w, u);   // u + k2 w
-          } else {
-            out = df_mad(k1, w, u);  // u + k1 w
-            wn = df_mad(k2, u, w);   // w + k2 u
-          }
-          w = wn;
-          ((double *)a.out_q[j])[row] = f22d(out);
-          st.put(qb + j, r, out);
-          mark(qb + j);
-        }
-      }
-      break;
+      w = wn;
+      ((double *)a.out_q[j])[row] = f22d(out);
+      st.put(qb + j, r, out);
+      mark(qb + j);
     }
-    case K_PROJ: {
-      const int qb = a.qbase;
-      F2 acc = d2f2(st.d(0)[r]);
-      const bool reorth = a.orth == O_DCGS2 && (a.flags & 0x100u);
-      const int kk = a.k - 1;
-      if (reorth) {
-        float p, e;
-        prod_ff(cfpair(cf, CF_MISC), d2f2(st.d(qb + kk)[r]), p, e);
-        F2 qn = fast_two_sum(p, e);
-        for (int j = 0; j < kk; ++j)
-          qn = df_mad(cfpair(cf, CF_COEF2 + 2 * j), d2f2(st.d(qb + j)[r]), qn);
-        ((double *)a.out_q[kk])[row] = f22d(qn);
-        st.put(qb + kk, r, qn);
-        mark(qb + kk);
-      }
-      for (int j = a.j0; j < a.k; ++j) {
-        const int c = qb + j - a.j0;
-        const F2 q = (reorth && c == qb + kk) ? st.f2(c, r) : d2f2(st.d(c)[r]);
-        acc = df_mad(cfpair(cf, CF_COEF + 2 * j), q, acc);
-      }
-      float p, e;
-      prod_ff(acc, cfpair(cf, CF_MISC + 2), p, e);
-      ((double *)a.out_q[a.k])[row] = f22d(fast_two_sum(p, e));
-      st.put(0, r, acc);
-      mark(0);
-      if (a.step_mode) {
-        st.put(1, r, d2f2(st.d(1)[r]));
-        mark(1);
-      }
-      break;
-    }
-    case K_CGS2B: {
-      F2 acc = d2f2(st.d(0)[r]);
-      for (int j = 0; j < a.k; ++j)
-        acc = df_mad(cfpair(cf, CF_COEF + 2 * j), d2f2(st.d(a.qbase + j)[r]), acc);
-      a.out_df[row] = f22d(acc);
-      st.put(0, r, acc);
-      mark(0);
-      break;
-    }
-    case K_MGS: {
-      const F2 acc = df_mad(cfpair(cf, CF_COEF + 2 * (a.jm - 1)), d2f2(st.d(a.qbase)[r]),
-                            d2f2(st.d(0)[r]));
-      a.out_df[row] = f22d(acc);
-      st.put(0, r, acc);
-      mark(0);
-      break;
-    }
-    case K_UPDATE: {
-      F2 acc = d2f2(st.d(0)[r]);
-      for (int i = 0; i < a.ng; ++i)
-        acc = df_mad(cfpair(cf, CF_COEF + 2 * i), d2f2(st.d(a.qbase + i)[r]), acc);
-      const double xn = f22d(acc);
-      a.out_x[row] = xn;
-      if (a.stop_kind == 1) {
-        st.put(1, r, d2f2(xn - st.d(1)[r]));
-        mark(1);
-      }
-      break;
-    }
-    case K_LSQ: {
-      st.put(0, r, d2f2(st.d(0)[r]));
-      mark(0);
-      break;
-    }
-    default:
-      break;
   }
 }
 
@@ -981,8 +900,8 @@ static __device__ void epilogue(const PassArgs &a, double *scratch, int lane) {
 // MODE 2: FP32/BF16 storage; row programs and dot products on the FP32/INT
 //         pipes (row_program_df), partial sums folded into FP64 every
 //         second tile.
-// MODE 3: FP64 storage with the row programs and dot products on the
-//         FP32/INT pipes (row_program_dd, AA_FLAG_DF_ARITH), partial sums
+// MODE 3: FP64 storage, first pass only (AA_FLAG_DF_ARITH): rotation and dot
+//         products on the FP32/INT pipes (row_program_dd), partial sums
 //         folded into FP64 every fourth tile.
 
 template <class QT, int DPW, int MODE = 0>

@@ -7,7 +7,11 @@ namespace aa {
 cudaError_t launch_pass_f64df(const PassArgs &a, int nsm, int *grid_out, cudaStream_t stream);
 
 cudaError_t launch_pass_f64(const PassArgs &a, int nsm, int *grid_out, cudaStream_t stream) {
-  if (a.flags & 0x10u) return launch_pass_f64df(a, nsm, grid_out, stream);
+  // AA_FLAG_DF_ARITH moves only the first pass (rotation, differences, first
+  // dot block: the FP64-pipe-bound one) to (hi, lo) float arithmetic; the
+  // projection and update passes, which split every FP64 operand and do one
+  // multiply-add with it, issue more slowly in that form than on the FP64 pipe.
+  if ((a.flags & 0x10u) && a.kind == K_A) return launch_pass_f64df(a, nsm, grid_out, stream);
   if (a.flags & 0x8u) return launch_qm<double, 1>(a, nsm, grid_out, stream);
   return launch_qm<double, 0>(a, nsm, grid_out, stream);
 }

@@ -240,7 +240,9 @@ def solve_batch(lams, srcs, s: int, *, x0=None, m: int = 10, max_iters: int = 10
 
 def train(net, X, U, *, epochs: int = 30, batch: int = 128, lr: float = 1e-3, seed: int = 0,
           log=None):
-    """Mini-batch Adam on MSE(net(X), U); X fp32 [N, IN_PAD], U fp32 [N, out]."""
+    """Mini-batch training on MSE(net(X), U) (Adam on the hidden layers,
+    momentum SGD on the output layer, both step sizes decayed along a cosine
+    to 5 %); X fp32 [N, IN_PAD], U fp32 [N, out]."""
     import torch
     N = X.shape[0]
     Xd = torch.from_numpy(X).cuda().to(torch.bfloat16)
@@ -248,6 +250,8 @@ def train(net, X, U, *, epochs: int = 30, batch: int = 128, lr: float = 1e-3, se
     rng = np.random.default_rng(seed)
     hist = []
     for ep in range(epochs):
+        # cosine decay of both step sizes to 5 % over the run
+        fac = 0.05 + 0.95 * 0.5 * (1.0 + np.cos(np.pi * ep / max(1, epochs)))
         perm = rng.permutation(N)
         tot = 0.0
         for b0 in range(0, N - batch + 1, batch):
@@ -256,7 +260,7 @@ def train(net, X, U, *, epochs: int = 30, batch: int = 128, lr: float = 1e-3, se
             yb = Ud.index_select(0, idx)
             Y = net.forward(xb)
             loss, dY = net.loss_and_grad(Y, yb)
-            net.adam_step(net.backward(dY), lr=lr)
+            net.adam_step(net.backward(dY), lr=lr * fac, lr_out=2e-4 * net.dims[3] * fac)
             tot += loss
         hist.append(tot / max(1, N // batch))
         if log:
