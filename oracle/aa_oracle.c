@@ -13,7 +13,7 @@
  * left-to-right loop in double precision; the file is compiled with
  * -ffp-contract=off so that no multiply-add is fused behind our back.
  *
- * Readings where the paper is silent or garbled (each restated in the design doc):
+ * Readings where the paper is silent or garbled:
  *  - QRDelete (Sec. 2.1, Sec. 3.2 text): textbook Givens column deletion.
  *  - ICWY after a delete (Sec. 3.2): the strictly-lower part of T is
  *    recomputed from the rotated Q in one reduction.

@@ -149,7 +149,7 @@ def test_step_parity_bratu_ragged(aa, ora, orth):
 
 
 @pytest.mark.parametrize("orth", VARIANTS)
-def test_solve_jacobi2d_config0(aa, ora, orth):
+def test_solve_jacobi2d_64_to_tol(aa, ora, orth):
     """The 64 x 64 workload to ||f||/||b|| < 1e-8: same iteration count (+-1)
     and the same solution."""
     nx = ny = 64
