@@ -125,3 +125,22 @@ def test_exp_fp32pipe_accuracy(aa):
     got = aa.exp_fp32pipe(sp).cpu().tolist()
     assert math.isnan(got[0]) and got[1] == math.inf and got[2] == 0.0
     assert got[3] == math.inf and got[4] == 0.0
+
+
+def test_batch_times_profile(aa):
+    """aa_batch_times: every solve has a start no later than its stop, the
+    earliest start is 0, and the latest stop lies within the launch's own
+    event time; a solve's span grows with its iteration count at a fixed size."""
+    sides = [40, 40, 40, 12]
+    lams = np.array([2.0, 4.0, 5.5, 3.0])
+    B = aa.Batch(sides, lams, m=10, max_iters=20000)
+    ms = B.solve(block=256, ctas_per_sm=1)
+    it, _, st = B.results()
+    t0, t1 = B.times()
+    assert np.all(st == 0)
+    assert t0.min() == 0.0 and np.all(t1 >= t0)
+    assert t1.max() <= ms * 1.05 + 0.05
+    same = [0, 1, 2]
+    order_it = np.argsort(it[same])
+    spans = (t1 - t0)[same]
+    assert np.all(np.diff(spans[order_it]) >= -0.02 * spans.max())
