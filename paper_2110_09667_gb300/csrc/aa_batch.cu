@@ -389,11 +389,22 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : (NT <= 256 ? 2 : 1)) batch
       };
       stageA(tid, 0);
       int sgA = 0;
+      // grid coordinates of row r = j s + i, advanced by NT rows per step
+      // without a division per row
+      int j = tid / s, i = tid - (tid / s) * s;
+      const int jstep = NT / s, istep = NT - (NT / s) * s;
       for (int r = tid; r < (int)n; r += NT, sgA ^= 1) {
+        if (r != tid) {
+          i += istep;
+          j += jstep;
+          if (i >= s) {
+            i -= s;
+            ++j;
+          }
+        }
         stageA(r + NT, sgA ^ 1);
         prefetch_rows(lane, r - lane + PF * NT, n, a.Q + off, a.N, (it == 0) ? 0 : c, Xc, FP, GP, src);
         cp_async_wait<1>();
-        const int j = r / s, i = r - j * s;
         const double x = SD(sgA, 0);
         const double w = i > 0 ? Xc[r - 1] : 0.0;
         const double e = i < s - 1 ? Xc[r + 1] : 0.0;
@@ -782,6 +793,7 @@ template <int NT>
 static cudaError_t launch_batch(const BArgs &a, int grid, cudaStream_t s) {
   if (a.m <= 4) return launch_mb<NT, 4>(a, grid, s);
   if (a.m <= 8) return launch_mb<NT, 8>(a, grid, s);
+  if (a.m <= 10) return launch_mb<NT, 10>(a, grid, s);
   if (a.m <= 12) return launch_mb<NT, 12>(a, grid, s);
   return launch_mb<NT, 16>(a, grid, s);
 }
@@ -791,10 +803,11 @@ static cudaError_t launch_batch(const BArgs &a, int grid, cudaStream_t s) {
 template <int NT>
 static cudaError_t smem_attr_nt() {
   cudaError_t e = cudaSuccess;
-  const int mbs[4] = {4, 8, 12, 16};
+  const int mbs[5] = {4, 8, 10, 12, 16};
   for (int mb : mbs) {
     const void *f = mb == 4    ? (const void *)batch_kernel<NT, 4>
                     : mb == 8  ? (const void *)batch_kernel<NT, 8>
+                    : mb == 10 ? (const void *)batch_kernel<NT, 10>
                     : mb == 12 ? (const void *)batch_kernel<NT, 12>
                                : (const void *)batch_kernel<NT, 16>;
     const cudaError_t r = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -321,3 +321,51 @@ def test_df_arith_rejects_other_modes(aa):
         aa.Anderson(100, 3, "icwy", "fp32", flags=aa.FLAG_DF_ARITH)
     with pytest.raises(aa.AAError):
         aa.Anderson(100, 3, "icwy", flags=aa.FLAG_DF_ARITH | aa.FLAG_FP32_DOTS)
+
+
+# ------------------------------------------- deep histories (the bench's m)
+
+@pytest.mark.parametrize("orth", VARIANTS)
+@pytest.mark.parametrize("m", [20, 50, 64])
+def test_qradd_deep_history(aa, ora, orth, m):
+    """QR factors after m + 6 adds (6 deletes) for the bench's history depths
+    and the largest one the library takes (64), on a ragged n.  The inputs
+    are well conditioned (independent uniform vectors), so the factors agree
+    to the same tolerance as at small m."""
+    n = 4097
+    V = aa_synth.uniform(70 + m, (m + 6) * n).reshape(m + 6, n)
+    O = ora.Oracle(n, m, orth)
+    G = aa.Anderson(n, m, orth)
+    for j in range(m + 6):
+        O.qradd(V[j])
+        G.qradd(dev(V[j]))
+    Qo, Ro, _ = O.get_qr()
+    Qg, Rg, _ = G.get_qr()
+    tol = 1e-10 if orth != "dcgs2" else 1e-8
+    assert np.max(np.abs(Rg - Ro)) <= tol * np.abs(Ro).max(), orth
+    assert np.max(np.abs(Qg - Qo)) <= tol, orth
+    if orth != "dcgs2":  # the literal DCGS-2 update is checked against the oracle only
+        assert np.max(np.abs(Qg.T @ Qg - np.eye(m))) <= 1e-12
+
+
+@pytest.mark.parametrize("orth", VARIANTS)
+def test_step_parity_jacobi2d_m20(aa, ora, orth):
+    """The bench's history depth on the 64 x 64 problem: 30 iterates
+    (10 with a delete)."""
+    nx = ny = 64
+    b = aa_synth.jacobi2d_rhs(0, nx, ny)
+    Gmap = lambda x: ora.g_jacobi2d(nx, ny, 0.01, b, x)
+    out, _ = run_steps(aa, ora, Gmap, nx * ny, 20, orth, 30)
+    for i, (xo, xg, fo, fg) in enumerate(out):
+        assert abs(fg - fo) <= 1e-10 * abs(fo), (i, fo, fg)
+        assert np.linalg.norm(xg - xo) <= 1e-10 * np.linalg.norm(xo), (i, orth)
+
+
+def test_create_rejects_bad_sizes(aa):
+    """Empty and oversized inputs are refused before any device work."""
+    with pytest.raises(aa.AAError):
+        aa.Anderson(0, 5, "icwy")
+    with pytest.raises(aa.AAError):
+        aa.Anderson(100, 65, "icwy")
+    with pytest.raises(aa.AAError):
+        aa.Anderson(100, 0, "icwy")
