@@ -317,6 +317,15 @@ int aa_f32_to_bf16(int64_t n, const float *x, void *y, void *stream);
 /* hi = bf16(x), lo = bf16(x - hi) for n values. */
 int aa_f32_split_bf16(int64_t n, const float *x, void *hi, void *lo, void *stream);
 
+/* Self-test of the bounded device-side wait used by every streaming pass:
+ * one kernel waits on an mbarrier that nothing completes, gives up after the
+ * wait's iteration limit (about a second) and reports it.  Returns
+ * AA_ETIMEOUT when the wait ran out and came back as a status (the expected
+ * result; the context stays usable), AA_OK if the wait completed, AA_ECUDA or
+ * AA_ENOMEM on a CUDA failure.  Synchronizes `stream`.  No counterpart in the
+ * paper. */
+int aa_selftest_wait_timeout(void *stream);
+
 /* Message for the last error on this thread. */
 const char *aa_last_error(void);
 const char *aa_strerror(int code);

@@ -345,3 +345,11 @@ def exp_fp32pipe(u):
     out = u.new_empty(u.shape)
     _check(_batch_lib().aa_exp_fp32pipe(u.numel(), _ptr(u), _ptr(out), _stream()))
     return out
+
+
+def selftest_wait_timeout() -> int:
+    """aa_selftest_wait_timeout: a device wait that nothing completes must run
+    out and come back as AA_ETIMEOUT (the expected return value)."""
+    L = lib()
+    L.aa_selftest_wait_timeout.argtypes = [C.c_void_p]
+    return int(L.aa_selftest_wait_timeout(_stream()))

@@ -96,11 +96,21 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait (about a second at most): on expiry the pass records
-// DEV_ETIMEOUT and the caller stops issuing work.
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Bounded wait: gives up once a second has passed on the device's global
+// timer (checked every 64 tries; try_wait itself suspends only for a short,
+// system-defined time), with an iteration cap as a second bound.  On expiry
+// the pass records DEV_ETIMEOUT and the caller stops issuing work.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
-  for (uint32_t i = 0; i < (1u << 22); ++i) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (uint32_t i = 0; i < (1u << 26); ++i) {
     if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 63u) == 63u && global_ns() - t0 > 1000000000ull) return false;
     if (i > 32) __nanosleep(256);
   }
   return false;
