@@ -37,6 +37,12 @@ EY, EZ, OMEGA = 0.1, 0.01, 0.8
 SLAB_NZ = 8  # oracle sample: 406 x 406 x 8 rows of the same stencil problem
 
 
+def size_label(args) -> str:
+    if (args.nx, args.ny, args.nz) == (NX, NY, NZ):
+        return "n=406^3~2^26"
+    return f"n={args.nx}x{args.ny}x{args.nz}={args.nx * args.ny * args.nz}"
+
+
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -51,6 +57,8 @@ def parse():
     p.add_argument("--df-arith", action="store_true",
                    help="FP64 storage with (hi, lo) float arithmetic on the FP32/INT pipes "
                         "(AA_FLAG_DF_ARITH)")
+    p.add_argument("--nx", type=int, default=NX)
+    p.add_argument("--ny", type=int, default=NY)
     p.add_argument("--nz", type=int, default=NZ)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
@@ -222,7 +230,7 @@ def run_ours(args, ws, rank, local):
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
-    nx, ny, nz = NX, NY, args.nz
+    nx, ny, nz = args.nx, args.ny, args.nz
     n = nx * ny * nz
     esz = {"fp64": 8, "fp32": 4, "bf16": 2}[args.storage]
     b_h = aa_synth.jacobi3d_rhs(0, nx, ny, nz)
@@ -300,7 +308,7 @@ def run_ours(args, ws, rank, local):
                 tr = json.load(f)
             mode = "_df" if args.df_arith else ("_f32dots" if args.fp32_dots else "")
             key = f"{args.orth}_{args.storage}{mode}_m{args.m}_{dom}"
-            if key in tr and args.nz == NZ:
+            if key in tr and (args.nx, args.ny, args.nz) == (NX, NY, NZ):
                 traffic = tr[key]["bytes_per_launch_full_n"]
         except Exception:
             traffic = None
@@ -337,7 +345,7 @@ def run_ours(args, ws, rank, local):
         return None
     value = job_rate(args.steps, ws, ms)
     line = {
-        "metric": f"AA iterations/s (3D 7-pt weighted Jacobi, n=406^3~2^26, m={args.m}, "
+        "metric": f"AA iterations/s (3D 7-pt weighted Jacobi, {size_label(args)}, m={args.m}, "
                   f"{args.orth.upper()})",
         "value": round(value, 3),
         "unit": "iter/s",
@@ -461,7 +469,7 @@ def oracle_sample(args, iters: int, warm: int):
 
     import aa_synth
     import oracle
-    nx, ny, nz = NX, NY, SLAB_NZ
+    nx, ny, nz = args.nx, args.ny, SLAB_NZ
     n = nx * ny * nz
     b = aa_synth.jacobi3d_rhs(0, nx, ny, nz)
     O = oracle.Oracle(n, args.m, args.orth, store_round={"fp64": 0, "fp32": 1, "bf16": 2}[args.storage])
@@ -481,12 +489,12 @@ def oracle_sample(args, iters: int, warm: int):
 
 def cpu_baseline(args):
     t, ns = oracle_sample(args, args.cpu_iters, 0)
-    n = NX * NY * args.nz
+    n = args.nx * args.ny * args.nz
     per_iter_full = statistics.median(t) * n / ns
     return {"value": round(1.0 / per_iter_full, 5), "unit": "iter/s", "cores": 1,
             "kind": "oracle",
             "sample": f"{len(t)} recycle AA({args.m}) {args.orth} iterations (G + step) of the "
-                      f"oracle on a {NX}x{NY}x{SLAB_NZ} slab of the same stencil problem "
+                      f"oracle on a {args.nx}x{args.ny}x{SLAB_NZ} slab of the same stencil problem "
                       f"(n={ns}), median time scaled by n to the full {n}-row workload",
             "slab_s_per_iter_median": round(statistics.median(t), 4),
             "slab_s_per_iter_min": round(min(t), 4)}
@@ -496,24 +504,24 @@ def run_reference(args, ws, rank):
     if rank != 0:
         return None
     t, ns = oracle_sample(args, args.steps, args.warmup)
-    n = NX * NY * args.nz
+    n = args.nx * args.ny * args.nz
     total_full = sum(t) * n / ns
     value = args.steps / total_full
     return {
         "impl": "reference",
-        "metric": f"AA iterations/s (3D 7-pt weighted Jacobi, n=406^3~2^26, m={args.m}, "
+        "metric": f"AA iterations/s (3D 7-pt weighted Jacobi, {size_label(args)}, m={args.m}, "
                   f"{args.orth.upper()})",
         "value": round(value, 5), "unit": "iter/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(total_full / args.steps * 1e3, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded SplitMix64 b ~ U(-1,1), x0 = 0)",
         "config": {"workload": f"AA({args.m}) {args.orth} on 3D 7-pt weighted Jacobi "
-                               f"{NX}x{NY}x{args.nz}, recycle iterations",
+                               f"{args.nx}x{args.ny}x{args.nz}, recycle iterations",
                    "n": n, "m": args.m, "orth": args.orth, "storage": args.storage},
         "cpu_baseline": {"value": round(value, 5), "unit": "iter/s", "cores": 1,
                          "kind": "oracle",
                          "sample": f"each step: one recycle iteration (G + step) of the CPU "
-                                   f"oracle on a {NX}x{NY}x{SLAB_NZ} slab (n={ns}), time scaled "
+                                   f"oracle on a {args.nx}x{args.ny}x{SLAB_NZ} slab (n={ns}), time scaled "
                                    f"by n to the full workload"},
         "e2e": {"value": round(value, 5), "unit": "iter/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
@@ -590,7 +598,7 @@ def run_to_tol(args, ws_, rank, local):
     import aa_synth
     import paper_2110_09667_gb300 as aa
     torch.cuda.set_device(local)
-    nx, ny, nz = NX, NY, args.nz
+    nx, ny, nz = args.nx, args.ny, args.nz
     n = nx * ny * nz
     b = torch.from_numpy(aa_synth.jacobi3d_rhs(0, nx, ny, nz)).cuda()
     P = aa.Jacobi3D(nx, ny, nz, EY, EZ, OMEGA, b.data_ptr())

@@ -901,6 +901,14 @@ static __device__ void epilogue(const PassArgs &a, double *scratch, int lane) {
   __syncwarp();
 }
 
+// Passes of the exact-FP64 form with at most RD dot products (projection,
+// update, MGS links, the first add) accumulate them in the row program's own
+// thread, row by row, instead of in a separate warp-per-dot phase: no second
+// barrier per tile and no warps idling while one or two warps sum the tile.
+// (The float-pair forms keep the dot phase: there the per-row compensated
+// sums measured slower.)
+constexpr int RD = 4;
+
 // ---------------------------------------------------------------- kernel
 //
 // MODE 0: FP64 storage, FP64 arithmetic throughout (exact FP64 path).
@@ -993,6 +1001,11 @@ __global__ void __launch_bounds__(NT) pass_kernel(const __grid_constant__ PassAr
 
   double acc[DPW];
   float accS[MODE ? DPW : 1], accC[MODE ? DPW : 1];
+  constexpr int NRD = (DPW == 1 && MODE == 0) ? RD : 1;
+  const bool rowdots = (DPW == 1) && (MODE == 0) && a.ndots <= RD;
+  double racc[NRD];
+#pragma unroll
+  for (int d = 0; d < NRD; ++d) racc[d] = 0.0;
 #pragma unroll
   for (int i = 0; i < DPW; ++i) acc[i] = 0.0;
   if constexpr (MODE != 0) {
@@ -1031,10 +1044,23 @@ __global__ void __launch_bounds__(NT) pass_kernel(const __grid_constant__ PassAr
         }
       }
     }
-    __syncthreads();
+    if constexpr (MODE == 0) {
+      if (rowdots && tid < rows) {
+#pragma unroll
+        for (int d = 0; d < NRD; ++d) {
+          if (d < a.ndots) {
+            const int ca = sda[d], cb = sdb[d];
+            racc[d] = fma(ldv<QT>(st, ca, tid, ca >= a.qbase), ldv<QT>(st, cb, tid, cb >= a.qbase),
+                          racc[d]);
+          }
+        }
+      }
+    }
+    if (!rowdots) __syncthreads();
     // dot phase: warp w owns dots w, w + NWARP, ...
 #pragma unroll
     for (int i = 0; i < DPW; ++i) {
+      if (rowdots) break;
       const int d = warp + NWARP * i;
       if (d < a.ndots) {
         const int ca = sda[d], cb = sdb[d];
@@ -1114,14 +1140,31 @@ __global__ void __launch_bounds__(NT) pass_kernel(const __grid_constant__ PassAr
   const bool has_epilogue = a.ndots > 0 || a.kind == K_A || a.kind == K_PROJ;
   if (!has_epilogue) return;
 
-  // Per-CTA partial sums (warp butterfly, fixed order).
+  // Per-CTA partial sums (warp butterfly, then warps in order: fixed order).
+  if (rowdots) {
+    __shared__ double rdw[NWARP][RD];
 #pragma unroll
-  for (int i = 0; i < DPW; ++i) {
-    const int d = warp + NWARP * i;
-    double v = acc[i];
+    for (int d = 0; d < NRD; ++d) {
+      double v = racc[d];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0 && d < a.ndots) a.partials[(size_t)blockIdx.x * NDOT_MAX + d] = v;
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) rdw[warp][d] = v;
+    }
+    __syncthreads();
+    if (tid < a.ndots) {
+      double v = 0.0;
+      for (int w = 0; w < NWARP; ++w) v += rdw[w][tid];
+      a.partials[(size_t)blockIdx.x * NDOT_MAX + tid] = v;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < DPW; ++i) {
+      const int d = warp + NWARP * i;
+      double v = acc[i];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0 && d < a.ndots) a.partials[(size_t)blockIdx.x * NDOT_MAX + d] = v;
+    }
   }
   __threadfence();
   __syncthreads();
