@@ -199,7 +199,7 @@ def pass_flops(kind: str, n: int, m: int, orth: str) -> float:
     """Algorithmic FP64 flops of one launch at a full history."""
     k = m - 1
     if kind == "A":
-        rot = 6 * (m - 1) + 1
+        rot = 4 * (m - 1)  # scaled Givens: two multiply-adds per rotation per row
         diffs = 3
         dots = 3 + 2 * k + (k - 1 if orth in ("icwy", "dcgs2") else 0)
         if orth == "mgs":

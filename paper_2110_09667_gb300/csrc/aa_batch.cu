@@ -444,15 +444,13 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : (NT <= 256 ? 2 : 1)) batch
             if (jj < m - 1) {
               const float u = qv[jj + 1];
               const F2 k1{cfr[4 * jj], cfr[4 * jj + 1]}, k2{cfr[4 * jj + 2], cfr[4 * jj + 3]};
-              F2 out, wn;
-              if (__double_as_longlong(st.rot[4 * jj + 2]) != 0) {
-                out = aa::df_axpy_f(wv, k1, u);
-                wn = aa::df_axpy_ff(u, k2, wv);
-              } else {
-                out = aa::df_axpy_ff(u, k1, wv);
-                wn = aa::df_axpy_f(wv, k2, u);
-              }
-              wv = wn;
+              // the two scaled-rotation forms as one: operands selected, so
+              // that exactly two (hi, lo) multiply-adds are issued
+              const bool ty = __double_as_longlong(st.rot[4 * jj + 2]) != 0;
+              const F2 P = aa::df_axpy_f(wv, ty ? k1 : k2, u);   // w + kp u
+              const F2 Qv = aa::df_axpy_ff(u, ty ? k2 : k1, wv);  // u + kq w
+              const F2 out = ty ? P : Qv;
+              wv = ty ? Qv : P;
               qv[jj] = out.h;
               a.Q[(int64_t)jj * a.N + off + r] = out.h;
             }

@@ -235,15 +235,17 @@ __device__ __forceinline__ void row_program(const PassArgs &a, Stage st, int t, 
         for (int j = 0; j < a.m - 1; ++j) {
           const double u = to_d<QT>(st.q<QT>(qb + j + 1)[r]);
           const double *R = co + CO_ROT + 4 * j;
-          double out, wn;
-          if (__double_as_longlong(R[2]) != 0) {  // |c| >= |s| (integer test: no FP64 op)
-            out = fma(R[0], u, w);
-            wn = fma(R[1], w, u);
-          } else {
-            out = fma(R[0], w, u);
-            wn = fma(R[1], u, w);
-          }
-          w = wn;
+          // The two forms (|c| >= |s| or not; integer test, no FP64 op)
+          // differ only in which multiplier goes with which operand and
+          // which result is kept: select those, so that exactly two
+          // multiply-adds are issued (a branch here may be if-converted
+          // into both forms, four multiply-adds).
+          const bool ty = __double_as_longlong(R[2]) != 0;
+          const double kp = ty ? R[0] : R[1], kq = ty ? R[1] : R[0];
+          const double P = fma(kp, u, w);   // w + kp u
+          const double Qv = fma(kq, w, u);  // u + kq w
+          const double out = ty ? P : Qv;
+          w = ty ? Qv : P;
           const QT qs = from_d<QT>(out);
           ((QT *)a.out_q[j])[row] = qs;
           st.q<QT>(qb + j)[r] = qs;
@@ -339,15 +341,12 @@ __device__ __forceinline__ void row_program_df(const PassArgs &a, Stage st, int 
           const float u = q2f<QT>(st.q<QT>(qb + j + 1)[r]);
           const float *R = cf + CF_ROT + 4 * j;
           const F2 k1{R[0], R[1]}, k2{R[2], R[3]};
-          F2 out, wn;
-          if (__double_as_longlong(co[CO_ROT + 4 * j + 2]) != 0) {
-            out = df_axpy_f(w, k1, u);
-            wn = df_axpy_ff(u, k2, w);
-          } else {
-            out = df_axpy_ff(u, k1, w);
-            wn = df_axpy_f(w, k2, u);
-          }
-          w = wn;
+          // both forms as one (operands selected, see row_program)
+          const bool ty = __double_as_longlong(co[CO_ROT + 4 * j + 2]) != 0;
+          const F2 P = df_axpy_f(w, ty ? k1 : k2, u);   // w + kp u
+          const F2 Qv = df_axpy_ff(u, ty ? k2 : k1, w);  // u + kq w
+          const F2 out = ty ? P : Qv;
+          w = ty ? Qv : P;
           const QT qs = f2q<QT>(out.h);
           ((QT *)a.out_q[j])[row] = qs;
           st.q<QT>(qb + j)[r] = qs;
@@ -459,15 +458,12 @@ __device__ __forceinline__ void row_program_dd(const PassArgs &a, Stage st, int 
     for (int j = 0; j < a.m - 1; ++j) {
       const F2 u = d2f2(st.d(qb + j + 1)[r]);
       const F2 k1 = cfpair(cf, CF_ROT + 4 * j), k2 = cfpair(cf, CF_ROT + 4 * j + 2);
-      F2 out, wn;
-      if (__double_as_longlong(co[CO_ROT + 4 * j + 2]) != 0) {
-        out = df_mad(k1, u, w);  // w + k1 u
-        wn = df_mad(k2, w, u);   // u + k2 w
-      } else {
-        out = df_mad(k1, w, u);  // u + k1 w
-        wn = df_mad(k2, u, w);   // w + k2 u
-      }
-      w = wn;
+      // both forms as one (operands selected, see row_program)
+      const bool ty = __double_as_longlong(co[CO_ROT + 4 * j + 2]) != 0;
+      const F2 P = df_mad(ty ? k1 : k2, u, w);   // w + kp u
+      const F2 Qv = df_mad(ty ? k2 : k1, w, u);  // u + kq w
+      const F2 out = ty ? P : Qv;
+      w = ty ? Qv : P;
       ((double *)a.out_q[j])[row] = f22d(out);
       st.put(qb + j, r, out);
       mark(qb + j);
