@@ -371,7 +371,11 @@ def run_ours(args, ws, rank, local):
                    "step": "G(x) + aa_step (pass A, projection, update)"},
         "roofline": roof,
         "passes": {kd: {"ms_avg": round(v["ms_avg"], 4), "launches": v["launches"],
-                        "share": round(v["ms_total"] / total_pass_ms, 4)}
+                        "share": round(v["ms_total"] / total_pass_ms, 4),
+                        "gbs_algorithmic": round(pass_bytes(kd, n, args.m, esz, args.orth)
+                                                 / (v["ms_avg"] * 1e-3) / 1e9, 1),
+                        "fp64_tflops_algorithmic": round(pass_flops(kd, n, args.m, args.orth)
+                                                         / (v["ms_avg"] * 1e-3) / 1e12, 4)}
                    for kd, v in per_kind.items()},
         "aa_passes_gbs": round(aa_gbs, 1) if aa_gbs else None,
         "aa_passes_ms_per_step": round(total_pass_ms / args.steps, 4),

@@ -369,3 +369,45 @@ def test_create_rejects_bad_sizes(aa):
         aa.Anderson(100, 65, "icwy")
     with pytest.raises(aa.AAError):
         aa.Anderson(100, 0, "icwy")
+
+
+def test_solve_python_callback_and_callback_error(aa, ora):
+    """aa_solve over a G written in Python (it forwards to the built-in 2D map
+    and counts its calls): the iterates equal those of the built-in callback;
+    a callback that returns non-zero stops the solve with AA_ECALLBACK after
+    exactly that call."""
+    nx = ny = 32
+    n = nx * ny
+    b = aa_synth.jacobi2d_rhs(0, nx, ny)
+    bd = dev(b)
+    P = aa.Jacobi2D(nx, ny, 0.01, bd.data_ptr())
+    inner = aa.builtin_g("aa_g_jacobi2d")
+    calls = []
+
+    def make(fail_at):
+        @aa.GFN
+        def g(x, gx, nn, stream, user):
+            calls.append(1)
+            if len(calls) == fail_at:
+                return 3
+            return inner(x, gx, nn, stream, user)
+        return g
+
+    A1 = aa.Anderson(n, 5, "icwy", max_iters=30, tol=1e-30)
+    x1 = torch.zeros(n, dtype=torch.float64, device="cuda")
+    rc1, st1 = A1.solve(inner, P, x1)
+    calls.clear()
+    g_ok = make(-1)
+    A2 = aa.Anderson(n, 5, "icwy", max_iters=30, tol=1e-30)
+    x2 = torch.zeros(n, dtype=torch.float64, device="cuda")
+    rc2, st2 = A2.solve(g_ok, P, x2)
+    assert rc1 == rc2 and st1["iters"] == st2["iters"]
+    assert torch.equal(x1, x2)
+    calls.clear()
+    g_bad = make(4)
+    A3 = aa.Anderson(n, 5, "icwy", max_iters=30, tol=1e-30)
+    x3 = torch.zeros(n, dtype=torch.float64, device="cuda")
+    with pytest.raises(aa.AAError) as e:
+        A3.solve(g_bad, P, x3)
+    assert e.value.code == -7
+    assert len(calls) == 4
