@@ -49,11 +49,11 @@ template <> __device__ __forceinline__ __nv_bfloat16 from_d<__nv_bfloat16>(doubl
 template <class QT> __device__ __forceinline__ float q2f(QT v);
 template <> __device__ __forceinline__ float q2f<float>(float v) { return v; }
 template <> __device__ __forceinline__ float q2f<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
-template <> __device__ __forceinline__ float q2f<double>(double v) { return (float)v; }  // unused
+template <> __device__ __forceinline__ float q2f<double>(double v) { return (float)v; }  // not called: FP64 paths split with d2f2
 template <class QT> __device__ __forceinline__ QT f2q(float v);
 template <> __device__ __forceinline__ float f2q<float>(float v) { return v; }
 template <> __device__ __forceinline__ __nv_bfloat16 f2q<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
-template <> __device__ __forceinline__ double f2q<double>(float v) { return (double)v; }  // unused
+template <> __device__ __forceinline__ double f2q<double>(float v) { return (double)v; }  // not called on FP64 paths
 
 // ------------------------------------------------- mbarrier / bulk copies
 
