@@ -144,3 +144,36 @@ def test_batch_times_profile(aa):
     order_it = np.argsort(it[same])
     spans = (t1 - t0)[same]
     assert np.all(np.diff(spans[order_it]) >= -0.02 * spans.max())
+
+
+def test_batch_full_size_sampled(aa, ora):
+    """The 4096-solve workload of the bench (sides log-uniform in [32, 256],
+    lambda ~ U(1, 6), zero source) in the bench's launch shape, capped at 3000
+    iterations: every solve either meets the stop rule (checked with the
+    oracle's FP64 map on 40 converged solves drawn at random) or stops at the
+    cap; on 8 capped solves the residual the kernel reports equals the
+    oracle's evaluation of the returned iterate."""
+    sides, lams = aa_synth.bratu_batch(0, 4096)
+    B = aa.Batch(sides, lams, m=10, tol=1e-8, max_iters=3000)
+    B.solve(512, 1)
+    it, rs, st = B.results()
+    assert set(np.unique(st)) <= {0, 1}
+    assert np.all(it[st == 1] == 3000) and np.all(it[st == 0] <= 3000)
+    rng = np.random.default_rng(5)
+    conv = np.flatnonzero(st == 0)
+    capped = np.flatnonzero(st == 1)
+    assert conv.size > 1000 and capped.size > 100
+    for i in rng.choice(conv, 40, replace=False):
+        s, lam = int(sides[i]), float(lams[i])
+        x = B.solution(int(i))
+        sc = scale_of(ora, s, lam, None)
+        res = np.linalg.norm(ora.g_bratu2d(s, lam, None, x) - x) / sc
+        assert res < 1.01e-8, (i, s, lam, res)
+    for i in rng.choice(capped, 8, replace=False):
+        s, lam = int(sides[i]), float(lams[i])
+        x = B.solution(int(i))
+        sc = scale_of(ora, s, lam, None)
+        res = np.linalg.norm(ora.g_bratu2d(s, lam, None, x) - x) / sc
+        # the kernel reports ||f|| of the returned iterate
+        assert abs(res - rs[i]) <= 1e-6 * res + 1e-14, (i, res, rs[i])
+        assert res >= 1e-8
