@@ -200,9 +200,16 @@ __device__ void prepare_delete_b(SState &st, int M, int lane) {
   double tau = st.sig[0];  // every lane carries the same value
   for (int j = 0; j + 1 < M; ++j) {
     const double av = st.Rn[j * BM + j], bv = st.Rn[(j + 1) * BM + j];
-    const double rho = hypot(av, bv);
+    // one reciprocal square root on the dependency chain; hypot and
+    // divisions only outside the normal range of a^2 + b^2
+    const double t2 = fma(av, av, bv * bv);
     double c = 1.0, s = 0.0;
-    if (rho != 0.0) {
+    if (t2 > 1e-290 && t2 < 1e290) {
+      const double ri = rsqrt(t2);
+      c = av * ri;
+      s = bv * ri;
+    } else if (av != 0.0 || bv != 0.0) {
+      const double rho = hypot(av, bv);
       c = av / rho;
       s = bv / rho;
     }
@@ -289,10 +296,9 @@ __device__ void finalize_b(SState &st, int m, int k, double rho, double vf, doub
     // R gamma = rhs by columns: lane j holds rhs_j minus the terms of the
     // unknowns found so far.
     double sj = (lane <= k) ? st.rhs[lane] : 0.0;
+    const double inv = (lane <= k) ? 1.0 / st.R[lane * BM + lane] : 0.0;  // in parallel
     for (int l = k; l >= 0; --l) {
-      double gl = 0.0;
-      if (lane == l) gl = sj / st.R[l * BM + l];
-      gl = __shfl_sync(0xffffffffu, gl, l);
+      const double gl = __shfl_sync(0xffffffffu, sj * inv, l);
       if (lane < l) sj -= st.R[lane * BM + l] * gl;
       if (lane == l) st.gam[l] = gl;
     }

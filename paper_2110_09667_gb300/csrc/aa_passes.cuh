@@ -514,10 +514,10 @@ static __device__ void mat_in(double *dst, const double *src, int M, int lane) {
   for (int i = lane; i < M * M; i += 32) dst[i] = src[(i / M) * MMAX + (i % M)];
   __syncwarp();
 }
+// (Entries outside the leading M x M block are never written after the
+// state is zeroed at creation and reset, and never read.)
 static __device__ void mat_out(double *dst, const double *src, int M, int lane) {
   for (int i = lane; i < M * M; i += 32) dst[(i / M) * MMAX + (i % M)] = src[i];
-  for (int i = lane; i < MMAX * MMAX; i += 32)
-    if ((i / MMAX) >= M || (i % MMAX) >= M) dst[i] = 0.0;
   __syncwarp();
 }
 static __device__ void vec_in(double *dst, const double *src, int n, int lane) {
@@ -529,26 +529,40 @@ static __device__ void vec_out(double *dst, const double *src, int n, int lane) 
   __syncwarp();
 }
 
+// The small triangular solves run by columns on warp 0: lane j keeps the
+// partial right-hand side of rows j and j + 32 (n <= 64) in registers, so a
+// step is one broadcast and one multiply-add instead of a warp reduction per
+// row (on GB300 a dependent FP64 operation costs many cycles, and the m x m
+// work sits on every pass's critical path).
+
 // Back substitution with an upper-triangular R (ld M): x = R^{-1} b, n unknowns.
+// The reciprocals of the diagonal are formed once, in parallel.
 static __device__ void backsolve(const Epi &e, const double *b, double *x, int n, int lane) {
-  for (int j = n - 1; j >= 0; --j) {
-    double p = 0.0;
-    for (int l = j + 1 + lane; l < n; l += 32) p += e.R[j * e.M + l] * x[l];
-    p = warp_sum(p);
-    if (lane == 0) x[j] = (b[j] - p) / e.R[j * e.M + j];
-    __syncwarp();
+  double s0 = (lane < n) ? b[lane] : 0.0, s1 = (lane + 32 < n) ? b[lane + 32] : 0.0;
+  const double i0 = (lane < n) ? 1.0 / e.R[lane * e.M + lane] : 0.0;
+  const double i1 = (lane + 32 < n) ? 1.0 / e.R[(lane + 32) * e.M + lane + 32] : 0.0;
+  for (int l = n - 1; l >= 0; --l) {
+    const double own = (l >= 32) ? s1 * i1 : s0 * i0;  // x_l, valid on lane l % 32
+    const double xl = __shfl_sync(0xffffffffu, own, l & 31);
+    if (lane == (l & 31)) x[l] = xl;
+    if (lane < l) s0 -= e.R[lane * e.M + l] * xl;
+    if (lane + 32 < l) s1 -= e.R[(lane + 32) * e.M + l] * xl;
   }
+  __syncwarp();
 }
 
 // Forward substitution with the unit-lower T (ld M): x = T^{-1} x in place.
 static __device__ void forward_unit(const Epi &e, double *x, int n, int lane) {
-  for (int j = 1; j < n; ++j) {
-    double p = 0.0;
-    for (int l = lane; l < j; l += 32) p += e.T[j * e.M + l] * x[l];
-    p = warp_sum(p);
-    if (lane == 0) x[j] -= p;
-    __syncwarp();
+  double v0 = (lane < n) ? x[lane] : 0.0, v1 = (lane + 32 < n) ? x[lane + 32] : 0.0;
+  for (int l = 0; l + 1 < n; ++l) {
+    const double xl = __shfl_sync(0xffffffffu, (l >= 32) ? v1 : v0, l & 31);
+    if (lane > l && lane < n) v0 -= e.T[lane * e.M + l] * xl;
+    if (lane + 32 > l && lane + 32 < n) v1 -= e.T[(lane + 32) * e.M + l] * xl;
   }
+  __syncwarp();
+  if (lane < n) x[lane] = v0;
+  if (lane + 32 < n) x[lane + 32] = v1;
+  __syncwarp();
 }
 
 // Givens parameters of the next QRDelete, computed from R alone: the rotated
@@ -587,9 +601,17 @@ static __device__ void prepare_delete(const PassArgs &a, DevState *S, const Epi 
   double tau = e.sig[0];  // scale of the carried column (lane 0 only)
   for (int j = 0; j + 1 < M; ++j) {
     const double av = e.r(j, j), bv = e.r(j + 1, j);
-    const double rho = hypot(av, bv);
+    // c = a / hypot(a, b), s = b / hypot(a, b) with one reciprocal square
+    // root (a short dependency chain); hypot and divisions only where
+    // a^2 + b^2 would leave the normal range
+    const double t2 = fma(av, av, bv * bv);
     double c = 1.0, s = 0.0;
-    if (rho != 0.0) {
+    if (t2 > 1e-290 && t2 < 1e290) {
+      const double ri = rsqrt(t2);
+      c = av * ri;
+      s = bv * ri;
+    } else if (av != 0.0 || bv != 0.0) {
+      const double rho = hypot(av, bv);
       c = av / rho;
       s = bv / rho;
     }
