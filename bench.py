@@ -61,6 +61,8 @@ def parse():
     p.add_argument("--ny", type=int, default=NY)
     p.add_argument("--nz", type=int, default=NZ)
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-variant", action="store_true",
+                   help="skip the FP32-pipe dot-product form measured beside the exact FP64 one")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-wall", action="store_true")
     p.add_argument("--cpu-iters", type=int, default=12)
@@ -337,6 +339,11 @@ def run_ours(args, ws, rank, local):
         e2e = run_e2e(args, A, gfn, Pp, n, dev, stream, one_step_state=(x, xn, g))
     wall = run_wall_to_tol(aa, args, dev) if (rank == 0 and not args.no_wall) else None
     startup = run_startup(A, one_step, x, stream, args.m)
+    variant = None
+    if (not args.no_variant and args.storage == "fp64" and not (args.fp32_dots or args.df_arith)):
+        del A
+        torch.cuda.empty_cache()
+        variant = run_variant(aa, args, gfn, Pp, n, dev, stream, esz, hbm_peak)
     if ws > 1:
         import torch.distributed as dist
         dist.barrier()
@@ -378,6 +385,7 @@ def run_ours(args, ws, rank, local):
                                                          / (v["ms_avg"] * 1e-3) / 1e12, 4)}
                    for kd, v in per_kind.items()},
         "aa_passes_gbs": round(aa_gbs, 1) if aa_gbs else None,
+        "aa_passes_hbm_frac": round(aa_gbs / hbm_peak, 4) if aa_gbs else None,
         "aa_passes_ms_per_step": round(total_pass_ms / args.steps, 4),
         "fnorm_last": fn,
         "gpu_launches": int(launches),
@@ -386,9 +394,56 @@ def run_ours(args, ws, rank, local):
         "wall_to_1e-8": wall,
         "startup": startup,
     }
+    if variant is not None:
+        line["fp32_pipe_dots"] = variant
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(args)
     return line
+
+
+def run_variant(aa, args, gfn, Pp, n, dev, stream, esz, hbm_peak):
+    """The same recycle steps with AA_FLAG_FP32_DOTS: FP64 storage and FP64
+    updates, the dot products of the first pass on the FP32 pipe (exact
+    products of (hi, lo) splits, compensated sums folded into FP64).  A fresh
+    context, filled and warmed up like the main one, timed over the same
+    number of steps with CUDA events on the launching stream."""
+    import torch
+    sp = stream.cuda_stream
+    A = aa.Anderson(n, args.m, args.orth, "fp64", flags=aa.FLAG_TIMING | aa.FLAG_FP32_DOTS,
+                    max_iters=10**6)
+    x = torch.zeros(n, dtype=torch.float64, device=dev)
+    xn = torch.empty_like(x)
+    g = torch.empty_like(x)
+    for i in range(args.m + 1 + args.warmup + args.steps):
+        if i == args.m + 1 + args.warmup:
+            torch.cuda.synchronize()
+            pt0 = A.pass_times()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+        if gfn(x.data_ptr(), g.data_ptr(), n, sp, Pp) != 0:
+            raise RuntimeError("G failed")
+        A.step(x, g, xn)
+        x, xn = xn, x
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    pt1 = A.pass_times()
+    passes, tot_ms, tot_bytes = {}, 0.0, 0.0
+    for kd, (tms, cnt) in pt1.items():
+        t0, c0 = pt0.get(kd, (0.0, 0))
+        if cnt - c0 > 0:
+            avg = (tms - t0) / (cnt - c0)
+            passes[kd] = round(avg, 4)
+            tot_ms += tms - t0
+            tot_bytes += pass_bytes(kd, n, args.m, esz, args.orth) * (cnt - c0)
+    gbs = tot_bytes / (tot_ms * 1e-3) / 1e9
+    del A, x, xn, g
+    torch.cuda.empty_cache()
+    return {"value": round(args.steps / (ms * 1e-3), 3), "unit": "iter/s",
+            "ms_per_step": round(ms / args.steps, 4), "passes_ms_avg": passes,
+            "aa_passes_gbs": round(gbs, 1), "aa_passes_hbm_frac": round(gbs / hbm_peak, 4),
+            "dtype": "f64 storage and updates; first-pass dot products on the FP32 pipe"}
 
 
 def run_startup(A, one_step, x, stream, m):

@@ -68,6 +68,31 @@ __device__ __forceinline__ F2 d2f2(double a) {
   return F2{__uint_as_float(hb), tl};
 }
 
+// Dot-product operand split: (hi, lo) floats of a * 2^s, with the power of
+// two s applied through the exponent field (exact).  Only the in-range case
+// of d2f2 is built: 2^-74 <= |a 2^s| < 2^128 gives hi + lo = a 2^s to 2^-48
+// relative; everything else (zero, smaller values, larger values, inf, nan)
+// becomes (0, 0).  Callers keep the operands near 1 by their choice of s and
+// test non-finite inputs separately.  sb = (128 + s) << 23 and
+// lim = (949 - s) << 20 are per-column constants (two's complement, s in
+// [-400, 400]).  Thirteen integer/FP32 operations, one of them on the
+// conversion unit.
+//   hb: the top 32 bits of a shifted left by 3 hold the low 8 exponent bits
+//   and the leading 23 significand bits; adding (128 + s) << 23 turns the
+//   low 8 bits of the double's exponent into the float's biased exponent
+//   (e - 896 + s, valid whenever that lies in [1, 254]).
+//   lo: the 29 remaining significand bits times 2^(E + s - 52), signed like a.
+__device__ __forceinline__ F2 d2f2_dot(double a, uint32_t sb, uint32_t lim) {
+  const uint32_t hi = (uint32_t)__double2hiint(a);
+  const uint32_t lo = (uint32_t)__double2loint(a);
+  const uint32_t t = __funnelshift_l(lo, hi, 3);
+  const uint32_t hb = ((t + sb) & 0x7fffffffu) | (hi & 0x80000000u);
+  const float sc = __uint_as_float((hb & 0xff800000u) - (52u << 23));
+  const float tl = __fmul_rn(__uint2float_rn(lo & 0x1fffffffu), sc);
+  const bool ok = ((hi & 0x7fffffffu) - lim) < (202u << 20);
+  return ok ? F2{__uint_as_float(hb), tl} : F2{0.f, 0.f};
+}
+
 // hi + lo -> double (one FP64 add; exact when the parts do not overlap).
 __device__ __forceinline__ double f22d(F2 a) { return f2d(a.h) + f2d(a.l); }
 

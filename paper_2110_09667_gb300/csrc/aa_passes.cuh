@@ -927,12 +927,51 @@ static __device__ void epilogue(const PassArgs &a, double *scratch, int lane) {
 // sums measured slower.)
 constexpr int RD = 4;
 
+// MODE 1 operand scaling.  The FP32-pipe products need operands well inside
+// the float range, so every split column is scaled by a power of two 2^s
+// (exact; the sums are scaled back by 2^-(s_a + s_b)).  Stored history
+// columns u_j (q_j = sig_j u_j, so ||u_j|| = 1 / sig_j) are brought to a
+// root-mean-square entry near 1.  The vectors f, Delta f (pass A) and y
+// (CGS-2 middle pass) are brought near 2^16 from the squared norm of the
+// previous pass A (f and Delta f of consecutive iterations have similar
+// sizes) or the current ||Delta f||^2: since |a 2^s| in [2^-74, 2^128) is
+// split exactly, a vector may be up to about 2^90 smaller or 2^47 larger
+// (cross products below 2^127) than that estimate.
+__device__ __forceinline__ int pow2_of_rms(double mean_sq, bool inverse, int centre) {
+  if (!(mean_sq > 0.0) || !(mean_sq < 1e300)) return centre;
+  const int ex = ((__double2hiint(mean_sq) >> 20) & 0x7ff) - 1023;  // floor(log2 mean_sq)
+  const int s = (inverse ? (ex >> 1) : -(ex >> 1)) + centre;
+  return max(-400, min(400, s));
+}
+
+static __device__ int dot_col_exp(const PassArgs &a, const DevState *S, int c) {
+  const double n = (double)a.n;
+  if (c < a.qbase) {
+    const double v2 = (a.kind == K_A && a.step_mode) ? S->st.fnorm2 : S->st.dfnorm2;
+    return pow2_of_rms(v2 / n, false, 16);
+  }
+  const int j = c - a.qbase;
+  if (j >= MMAX) return 0;
+  const double sg = (a.kind == K_A && a.del) ? (j < a.m - 1 ? S->rot[4 * j + 3] : 0.0) : S->sig[j];
+  // mean square of u_j = 1 / (sig_j^2 n): scale by sqrt(sig_j^2 n)
+  return pow2_of_rms(sg * sg * n, true, 0);
+}
+
+// 2^e as a double, e in [-1022, 1023] (exact).
+__device__ __forceinline__ double pow2d(int e) {
+  return __hiloint2double((1023 + e) << 20, 0);
+}
+
 // ---------------------------------------------------------------- kernel
 //
 // MODE 0: FP64 storage, FP64 arithmetic throughout (exact FP64 path).
-// MODE 1: FP64 storage and FP64 row programs; dot products on the FP32
-//         pipe from (hi, lo) splits, accumulated per lane in compensated
-//         float pairs and folded into FP64 once per tile.
+// MODE 1: FP64 storage and FP64 row programs (rotation, differences, all
+//         stored values exact FP64), for passes with more than RD dot
+//         products (AA_FLAG_FP32_DOTS): the leading squared norms of vectors
+//         stay FP64 row-local sums (they also carry the non-finite test);
+//         the other dot products run on the FP32 pipe from scaled (hi, lo)
+//         splits (d2f2_dot), exact head products, compensated per-lane
+//         float-pair sums folded into FP64 every eighth tile.
 // MODE 2: FP32/BF16 storage; row programs and dot products on the FP32/INT
 //         pipes (row_program_df), partial sums folded into FP64 every
 //         second tile.
@@ -949,6 +988,12 @@ __global__ void __launch_bounds__(NT) pass_kernel(const __grid_constant__ PassAr
   __shared__ uint8_t sda[NDOT_MAX], sdb[NDOT_MAX];
   __shared__ int s_last;
   __shared__ int s_err;
+  // MODE 1: per-column split constants and scale exponents, the columns to
+  // split, and the number of leading FP64 squared-norm dots
+  __shared__ uint32_t s_sb[MODE == 1 ? MAXCOL : 1], s_lim[MODE == 1 ? MAXCOL : 1];
+  __shared__ int s_cexp[MODE == 1 ? MAXCOL : 1];
+  __shared__ uint64_t s_split[2];
+  __shared__ int s_n64;
 
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
@@ -962,6 +1007,27 @@ __global__ void __launch_bounds__(NT) pass_kernel(const __grid_constant__ PassAr
     sdb[d] = a.dot_b[d];
   }
   if (tid == 0) s_err = 0;
+  if constexpr (MODE == 1) {
+    for (int c = tid; c < a.ncol; c += NT) {
+      const int e = dot_col_exp(a, S, c);
+      s_cexp[c] = e;
+      s_sb[c] = (uint32_t)(128 + e) << 23;
+      s_lim[c] = (uint32_t)(949 - e) << 20;
+    }
+    if (tid == 0) {
+      int n64 = 0;
+      while (n64 < a.ndots && n64 < RD && a.dot_a[n64] == a.dot_b[n64] && a.dot_a[n64] < a.qbase)
+        ++n64;
+      uint64_t sm[2] = {0ull, 0ull};
+      for (int d = n64; d < a.ndots; ++d) {
+        sm[a.dot_a[d] >> 6] |= 1ull << (a.dot_a[d] & 63);
+        sm[a.dot_b[d] >> 6] |= 1ull << (a.dot_b[d] & 63);
+      }
+      s_split[0] = sm[0];
+      s_split[1] = sm[1];
+      s_n64 = n64;
+    }
+  }
   __syncthreads();
   if (a.kind == K_A && a.del) {
     for (int i = tid; i < 4 * (a.m - 1); i += NT) co[CO_ROT + i] = S->rot[i];
@@ -1019,8 +1085,10 @@ __global__ void __launch_bounds__(NT) pass_kernel(const __grid_constant__ PassAr
 
   double acc[DPW];
   float accS[MODE ? DPW : 1], accC[MODE ? DPW : 1];
-  constexpr int NRD = (DPW == 1 && MODE == 0) ? RD : 1;
+  constexpr int NRD = ((DPW == 1 && MODE == 0) || MODE == 1) ? RD : 1;
   const bool rowdots = (DPW == 1) && (MODE == 0) && a.ndots <= RD;
+  // first dot of the warp-per-dot phase (MODE 1: after the FP64 norms)
+  const int dbase = (MODE == 1) ? s_n64 : 0;
   double racc[NRD];
 #pragma unroll
   for (int d = 0; d < NRD; ++d) racc[d] = 0.0;
@@ -1030,7 +1098,7 @@ __global__ void __launch_bounds__(NT) pass_kernel(const __grid_constant__ PassAr
 #pragma unroll
     for (int i = 0; i < DPW; ++i) accS[i] = accC[i] = 0.f;
   }
-  constexpr int FLUSH = (MODE == 2) ? 2 : (MODE == 3 ? 4 : 1);  // tiles per fold into FP64
+  constexpr int FLUSH = (MODE == 2) ? 2 : (MODE == 3 ? 4 : 8);  // tiles per fold into FP64
 
   int it = 0;
   for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++it) {
@@ -1056,9 +1124,18 @@ __global__ void __launch_bounds__(NT) pass_kernel(const __grid_constant__ PassAr
       } else {
         row_program<QT>(a, st, t, tid, co);
         if constexpr (MODE == 1) {
-          // the columns that feed the dot phase, as (hi, lo) floats
+          // FP64 squared norms, then the columns that feed the FP32-pipe
+          // dot phase as scaled (hi, lo) floats (in place)
+#pragma unroll
+          for (int d = 0; d < NRD; ++d) {
+            if (d < dbase) {
+              const double v = st.d(a.dot_a[d])[tid];
+              racc[d] = fma(v, v, racc[d]);
+            }
+          }
           for (int c = 0; c < a.ncol; ++c)
-            if ((a.dotcols[c >> 6] >> (c & 63)) & 1ull) st.put(c, tid, d2f2(st.d(c)[tid]));
+            if ((s_split[c >> 6] >> (c & 63)) & 1ull)
+              st.put(c, tid, d2f2_dot(st.d(c)[tid], s_sb[c], s_lim[c]));
         }
       }
     }
@@ -1079,7 +1156,7 @@ __global__ void __launch_bounds__(NT) pass_kernel(const __grid_constant__ PassAr
 #pragma unroll
     for (int i = 0; i < DPW; ++i) {
       if (rowdots) break;
-      const int d = warp + NWARP * i;
+      const int d = dbase + warp + NWARP * i;
       if (d < a.ndots) {
         const int ca = sda[d], cb = sdb[d];
         if constexpr (MODE == 0) {
@@ -1104,6 +1181,12 @@ __global__ void __launch_bounds__(NT) pass_kernel(const __grid_constant__ PassAr
               prod_f(st.f2(cv, r), q2f<QT>(st.q<QT>(cq)[r]), p, e);
               acc_add(S, C, p, e);
             }
+          } else if (MODE == 1 && rows == TR) {
+#pragma unroll
+            for (int q = 0; q < TR / 32; ++q) {
+              prod_ff(st.f2(ca, lane + 32 * q), st.f2(cb, lane + 32 * q), p, e);
+              acc_add(S, C, p, e);
+            }
           } else {
             for (int r = lane; r < rows; r += 32) {
               prod_ff(st.f2(ca, r), st.f2(cb, r), p, e);
@@ -1119,7 +1202,7 @@ __global__ void __launch_bounds__(NT) pass_kernel(const __grid_constant__ PassAr
       if ((it + 1) % FLUSH == 0) {
 #pragma unroll
         for (int i = 0; i < DPW; ++i) {
-          if (warp + NWARP * i < a.ndots) {
+          if (dbase + warp + NWARP * i < a.ndots) {
             acc[i] += f2d(accS[i]);
             acc[i] += f2d(accC[i]);
             accS[i] = accC[i] = 0.f;
@@ -1139,7 +1222,7 @@ __global__ void __launch_bounds__(NT) pass_kernel(const __grid_constant__ PassAr
   if constexpr (MODE != 0) {
 #pragma unroll
     for (int i = 0; i < DPW; ++i) {
-      if (warp + NWARP * i < a.ndots) {
+      if (dbase + warp + NWARP * i < a.ndots) {
         acc[i] += f2d(accS[i]);
         acc[i] += f2d(accC[i]);
       }
@@ -1159,7 +1242,8 @@ __global__ void __launch_bounds__(NT) pass_kernel(const __grid_constant__ PassAr
   if (!has_epilogue) return;
 
   // Per-CTA partial sums (warp butterfly, then warps in order: fixed order).
-  if (rowdots) {
+  if (rowdots || MODE == 1) {
+    const int nrow = (MODE == 1) ? dbase : a.ndots;
     __shared__ double rdw[NWARP][RD];
 #pragma unroll
     for (int d = 0; d < NRD; ++d) {
@@ -1169,19 +1253,23 @@ __global__ void __launch_bounds__(NT) pass_kernel(const __grid_constant__ PassAr
       if (lane == 0) rdw[warp][d] = v;
     }
     __syncthreads();
-    if (tid < a.ndots) {
+    if (tid < nrow) {
       double v = 0.0;
       for (int w = 0; w < NWARP; ++w) v += rdw[w][tid];
       a.partials[(size_t)blockIdx.x * NDOT_MAX + tid] = v;
     }
-  } else {
+  }
+  if (!rowdots) {
 #pragma unroll
     for (int i = 0; i < DPW; ++i) {
-      const int d = warp + NWARP * i;
+      const int d = dbase + warp + NWARP * i;
       double v = acc[i];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane == 0 && d < a.ndots) a.partials[(size_t)blockIdx.x * NDOT_MAX + d] = v;
+      if (lane == 0 && d < a.ndots) {
+        if constexpr (MODE == 1) v *= pow2d(-(s_cexp[a.dot_a[d]] + s_cexp[a.dot_b[d]]));
+        a.partials[(size_t)blockIdx.x * NDOT_MAX + d] = v;
+      }
     }
   }
   __threadfence();
@@ -1230,36 +1318,67 @@ static cudaError_t launch_t(const PassArgs &a, int grid, size_t smem, int nstage
 
 template <class QT, int DPW, int MODE>
 static int occupancy_t(size_t smem) {
+  // resident CTAs per SM for this instantiation and dynamic shared memory
+  // size, cached per host thread (the query sits on every pass launch)
+  thread_local size_t key[8];
+  thread_local int val[8];
+  thread_local int used = 0;
+  for (int i = 0; i < used; ++i)
+    if (key[i] == smem) return val[i];
   int nb = 0;
   auto kern = pass_kernel<QT, DPW, MODE>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024 - 8 * 1024);
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, NT, smem) != cudaSuccess) return 1;
-  return nb < 1 ? 1 : nb;
+  nb = nb < 1 ? 1 : nb;
+  if (used < 8) {
+    key[used] = smem;
+    val[used++] = nb;
+  }
+  return nb;
 }
 
-template <class QT, int MODE>
-static inline cudaError_t launch_qm(const PassArgs &a, int nsm, int *grid_out, cudaStream_t stream) {
+// Tile pipeline depth and grid of one pass.  Two stages (the next tile's
+// copies in flight while the current one is processed) unless they would
+// cut the resident CTAs per SM below min(one-stage occupancy, 4): several
+// CTAs at different points of their tile loop overlap copies with compute
+// as well, and more of them overlap the FP64 row programs of some with the
+// FP32-pipe dot phases of others.  The first pass of the exact FP64 form,
+// bound by the FP64 pipe, keeps two stages whenever they fit.  (Measured at
+// n = 406^3 for m = 5, 10, 20, 50.)
+template <class QT, int DPW, int MODE>
+static cudaError_t launch_shape(const PassArgs &a, int nsm, int *grid_out, cudaStream_t stream) {
   const size_t stage = (size_t)a.ncol * TR * 8;
   const size_t budget = 227 * 1024 - 8 * 1024;
-  int nstages = (stage * STAGES <= budget) ? STAGES : 1;
-  size_t smem = stage * nstages;
   const size_t epi = epi_doubles(a.m > 0 ? a.m : 1) * sizeof(double);
-  if (smem < epi) smem = epi;
-  if (smem > budget) return cudaErrorInvalidConfiguration;
-  int occ;
-  const int dpw_need = (a.ndots + NWARP - 1) / NWARP;
-  if (dpw_need <= 1) occ = occupancy_t<QT, 1, MODE>(smem);
-  else if (dpw_need <= 4) occ = occupancy_t<QT, 4, MODE>(smem);
-  else if (dpw_need <= 16) occ = occupancy_t<QT, 16, MODE>(smem);
-  else occ = occupancy_t<QT, 32, MODE>(smem);
+  const size_t smem1 = stage < epi ? epi : stage;
+  const size_t smem2 = 2 * stage < epi ? epi : 2 * stage;
+  if (smem1 > budget) return cudaErrorInvalidConfiguration;
+  int nstages = 1, occ = occupancy_t<QT, DPW, MODE>(smem1);
+  if (STAGES >= 2 && smem2 <= budget) {
+    const int occ2 = occupancy_t<QT, DPW, MODE>(smem2);
+    if (occ2 >= (occ < 4 ? occ : 4) || (MODE == 0 && a.kind == K_A)) {
+      nstages = 2;
+      occ = occ2;
+    }
+  }
   int grid = nsm * occ;
   if (grid > a.ntiles) grid = a.ntiles;
   if (grid < 1) grid = 1;
   *grid_out = grid;
-  if (dpw_need <= 1) return launch_t<QT, 1, MODE>(a, grid, smem, nstages, stream);
-  if (dpw_need <= 4) return launch_t<QT, 4, MODE>(a, grid, smem, nstages, stream);
-  if (dpw_need <= 16) return launch_t<QT, 16, MODE>(a, grid, smem, nstages, stream);
-  return launch_t<QT, 32, MODE>(a, grid, smem, nstages, stream);
+  return launch_t<QT, DPW, MODE>(a, grid, nstages == 2 ? smem2 : smem1, nstages, stream);
+}
+
+template <class QT, int MODE>
+static inline cudaError_t launch_qm(const PassArgs &a, int nsm, int *grid_out, cudaStream_t stream) {
+  const int dpw_need = (a.ndots + NWARP - 1) / NWARP;
+  if (dpw_need <= 1) return launch_shape<QT, 1, MODE>(a, nsm, grid_out, stream);
+  if (dpw_need <= 4) return launch_shape<QT, 4, MODE>(a, nsm, grid_out, stream);
+  if constexpr (MODE == 1) {
+    // an exact bucket for up to 8 dots per warp (m = 20 ICWY: 56)
+    if (dpw_need <= 8) return launch_shape<QT, 8, MODE>(a, nsm, grid_out, stream);
+  }
+  if (dpw_need <= 16) return launch_shape<QT, 16, MODE>(a, nsm, grid_out, stream);
+  return launch_shape<QT, 32, MODE>(a, nsm, grid_out, stream);
 }
 
 }  // namespace aa

@@ -12,7 +12,11 @@ cudaError_t launch_pass_f64(const PassArgs &a, int nsm, int *grid_out, cudaStrea
   // projection and update passes, which split every FP64 operand and do one
   // multiply-add with it, issue more slowly in that form than on the FP64 pipe.
   if ((a.flags & 0x10u) && a.kind == K_A) return launch_pass_f64df(a, nsm, grid_out, stream);
-  if (a.flags & 0x8u) return launch_qm<double, 1>(a, nsm, grid_out, stream);
+  // AA_FLAG_FP32_DOTS: the first pass of an add and the CGS-2 middle pass,
+  // when they carry more than RD dot products, move those products to the
+  // FP32 pipe; passes with a few products keep their FP64 row-local sums.
+  if ((a.flags & 0x8u) && a.ndots > RD && (a.kind == K_A || a.kind == K_CGS2B))
+    return launch_qm<double, 1>(a, nsm, grid_out, stream);
   return launch_qm<double, 0>(a, nsm, grid_out, stream);
 }
 }  // namespace aa

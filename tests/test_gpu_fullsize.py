@@ -109,3 +109,12 @@ def test_fullsize_recycle_step_df_arith(aa):
     err, scale, kappa, xnorm, _ = run(aa, "icwy", aa.FLAG_DF_ARITH)
     tol = 64 * kappa * 2.0 ** -48 * scale + 1e-12 * xnorm
     assert err <= tol, (err, tol, kappa)
+
+
+@pytest.mark.parametrize("orth", ["icwy", "cgs2"])
+def test_fullsize_recycle_step_fp32_dots(aa, orth):
+    """AA_FLAG_FP32_DOTS at full size: FP32-pipe dot products in the first
+    pass (and the CGS-2 middle pass), about 2^-46 of sum |a_i b_i| each."""
+    err, scale, kappa, xnorm, _ = run(aa, orth, aa.FLAG_FP32_DOTS)
+    tol = 64 * kappa * 2.0 ** -46 * scale + 1e-12 * xnorm
+    assert err <= tol, (orth, err, tol, kappa)

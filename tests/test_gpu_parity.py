@@ -232,9 +232,11 @@ def test_stagnation_breakdown_falls_back(aa, ora):
 
 @pytest.mark.parametrize("orth", VARIANTS)
 def test_step_parity_fp32_dots(aa, ora, orth):
-    """AA_FLAG_FP32_DOTS keeps the FP64 parity contract: the dot products
-    are formed on the FP32 pipe from (hi, lo) splits (error <= 2^-45 per
-    8-row group relative to sum |a_i b_i|) and accumulated in FP64."""
+    """AA_FLAG_FP32_DOTS keeps the FP64 parity contract: the dot products of
+    passes with more than four of them are formed on the FP32 pipe from
+    scaled (hi, lo) splits (exact head products, compensated float-pair
+    sums over 64 rows per lane, error about 2^-46 of sum |a_i b_i|) and
+    accumulated in FP64; squared norms stay FP64."""
     nx = ny = 64
     b = aa_synth.jacobi2d_rhs(0, nx, ny)
     Gmap = lambda x: ora.g_jacobi2d(nx, ny, 0.01, b, x)
@@ -258,6 +260,57 @@ def test_qradd_fp32_dots(aa, ora, orth):
         tol = 1e-11 if orth != "dcgs2" else 1e-9
         assert np.max(np.abs(Rg - Ro)) <= tol * np.abs(Ro).max(), (j, orth)
         assert np.max(np.abs(Qg - Qo)) <= tol, (j, orth)
+
+
+@pytest.mark.parametrize("orth", VARIANTS)
+def test_step_parity_fp32_dots_m20(aa, ora, orth):
+    """AA_FLAG_FP32_DOTS at the bench's history depth: 30 iterates, 10 of them
+    with a delete, to the FP64 contract."""
+    nx = ny = 64
+    b = aa_synth.jacobi2d_rhs(0, nx, ny)
+    Gmap = lambda x: ora.g_jacobi2d(nx, ny, 0.01, b, x)
+    out, _ = run_steps(aa, ora, Gmap, nx * ny, 20, orth, 30, flags=aa.FLAG_FP32_DOTS)
+    for i, (xo, xg, fo, fg) in enumerate(out):
+        assert abs(fg - fo) <= 1e-10 * abs(fo), (i, fo, fg)
+        assert np.linalg.norm(xg - xo) <= 1e-10 * np.linalg.norm(xo), (i, orth)
+
+
+@pytest.mark.parametrize("orth", VARIANTS)
+@pytest.mark.parametrize("m", [20, 50])
+def test_qradd_fp32_dots_deep(aa, ora, orth, m):
+    """QR factors with FP32-pipe dot products after m + 6 adds, ragged n."""
+    n = 4097
+    V = aa_synth.uniform(80 + m, (m + 6) * n).reshape(m + 6, n)
+    O = ora.Oracle(n, m, orth)
+    G = aa.Anderson(n, m, orth, flags=aa.FLAG_FP32_DOTS)
+    for j in range(m + 6):
+        O.qradd(V[j])
+        G.qradd(dev(V[j]))
+    Qo, Ro, _ = O.get_qr()
+    Qg, Rg, _ = G.get_qr()
+    tol = 1e-10 if orth != "dcgs2" else 1e-8
+    assert np.max(np.abs(Rg - Ro)) <= tol * np.abs(Ro).max(), orth
+    assert np.max(np.abs(Qg - Qo)) <= tol, orth
+
+
+@pytest.mark.parametrize("orth", ["icwy", "cgs2"])
+@pytest.mark.parametrize("scale", [1e-30, 1e30])
+def test_qradd_fp32_dots_far_from_one(aa, ora, orth, scale):
+    """Inputs far outside the float range's comfortable middle: the operands
+    of the FP32-pipe products are scaled by powers of two (exact) chosen from
+    the previous norms, so tiny and huge columns give the oracle's factors
+    (R scales with the input, Q does not)."""
+    n, m = 4097, 6
+    V = scale * aa_synth.uniform(90, (m + 3) * n).reshape(m + 3, n)
+    O = ora.Oracle(n, m, orth)
+    G = aa.Anderson(n, m, orth, flags=aa.FLAG_FP32_DOTS)
+    for j in range(m + 3):
+        O.qradd(V[j])
+        G.qradd(dev(V[j]))
+        Qo, Ro, _ = O.get_qr()
+        Qg, Rg, _ = G.get_qr()
+        assert np.max(np.abs(Rg - Ro)) <= 1e-11 * np.abs(Ro).max(), (j, orth)
+        assert np.max(np.abs(Qg - Qo)) <= 1e-11, (j, orth)
 
 
 # ------------------------- FP64 storage, (hi, lo) float arithmetic (MODE 3)
