@@ -60,10 +60,19 @@ typedef enum { AA_STORE_FP64 = 0, AA_STORE_FP32 = 1, AA_STORE_BF16 = 2 } aa_stor
                                       the rotated Q (fused into the first pass, k <= 24) instead
                                       of rotating T at the m x m level */
 #define AA_FLAG_TIMING 0x4u        /* record CUDA events around every pass (aa_pass_times) */
-#define AA_FLAG_FP32_DOTS 0x8u     /* FP64 storage: dot products on the FP32 pipe from (hi, lo)
-                                      splits of the FP64 operands (error <= 2^-45 sum|a_i b_i|
-                                      per tile), accumulated in FP64 across tiles; updates of
-                                      Q, v and x stay FP64 */
+#define AA_FLAG_FP32_DOTS 0x8u     /* FP64 storage: the dot products of the first pass of each
+                                      QR update (and of the CGS-2 middle pass), when there are
+                                      more than four, run on the FP32 pipe: exact products of
+                                      (hi, lo) float splits of the FP64 operands (each scaled by
+                                      a power of two, 2^-48 relative), compensated float-pair
+                                      sums over 64 rows per lane, folded into FP64.  Squared
+                                      norms of f and Delta f stay FP64 (they carry the NaN/Inf
+                                      test); Q, v, x, R, T and gamma stay FP64.  The scale of f
+                                      and Delta f is taken from the previous ||f|| (aa_step) or
+                                      ||Delta f|| (aa_qradd): a vector more than about 2^90
+                                      smaller or 2^47 larger than that loses its smallest or
+                                      overflows its cross products.  No counterpart in the
+                                      paper. */
 #define AA_FLAG_DF_ARITH 0x10u     /* FP64 storage: the first pass of each QR update (QRDelete
                                       rotation, first block of dot products) on the FP32/INT
                                       pipes in (hi, lo) float arithmetic, about 2^-48 relative
