@@ -464,3 +464,71 @@ def test_solve_python_callback_and_callback_error(aa, ora):
         A3.solve(g_bad, P, x3)
     assert e.value.code == -7
     assert len(calls) == 4
+
+
+# ------------------------------------------------------- built-in maps G
+
+@pytest.mark.parametrize("shape", [(1, 1), (37, 23), (64, 64), (130, 5)])
+def test_builtin_jacobi2d_matches_oracle(aa, ora, shape):
+    """The device map evaluates G = x + D^{-1}(b - A x) with the diagonal
+    term cancelled; it equals the oracle's literal form to a few roundings."""
+    nx, ny = shape
+    n = nx * ny
+    b = aa_synth.jacobi2d_rhs(3, nx, ny)
+    x = aa_synth.uniform(4, n)
+    bd, xd = dev(b), dev(x)
+    gd = torch.empty_like(xd)
+    P = aa.Jacobi2D(nx, ny, 0.01, bd.data_ptr())
+    rc = aa.builtin_g("aa_g_jacobi2d")(xd.data_ptr(), gd.data_ptr(), n,
+                                         torch.cuda.current_stream().cuda_stream,
+                                         aa.C.cast(aa.C.pointer(P), aa.C.c_void_p))
+    assert rc == 0
+    ref = ora.g_jacobi2d(nx, ny, 0.01, b, x)
+    scale = np.abs(x).max() + np.abs(b).max()
+    assert np.max(np.abs(gd.cpu().numpy() - ref)) <= 1e-14 * scale
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (19, 13, 7), (33, 2, 40), (406, 406, 3)])
+def test_builtin_jacobi3d_matches_oracle(aa, ora, shape):
+    """The bench's map, (1 - omega) x + (omega/d)(b + neighbour sums), against
+    the oracle's x + omega D^{-1}(b - A x), ragged sizes and the bench's plane."""
+    nx, ny, nz = shape
+    n = nx * ny * nz
+    b = aa_synth.jacobi3d_rhs(5, nx, ny, nz)
+    x = aa_synth.uniform(6, n)
+    bd, xd = dev(b), dev(x)
+    gd = torch.empty_like(xd)
+    P = aa.Jacobi3D(nx, ny, nz, 0.1, 0.01, 0.8, bd.data_ptr())
+    rc = aa.builtin_g("aa_g_jacobi3d")(xd.data_ptr(), gd.data_ptr(), n,
+                                         torch.cuda.current_stream().cuda_stream,
+                                         aa.C.cast(aa.C.pointer(P), aa.C.c_void_p))
+    assert rc == 0
+    ref = ora.g_jacobi3d(nx, ny, nz, 0.1, 0.01, 0.8, b, x)
+    scale = np.abs(x).max() + np.abs(b).max()
+    assert np.max(np.abs(gd.cpu().numpy() - ref)) <= 1e-14 * scale
+
+
+@pytest.mark.parametrize("s,with_src", [(1, False), (45, False), (45, True), (130, True)])
+def test_builtin_bratu2d_matches_oracle(aa, ora, s, with_src):
+    n = s * s
+    u = 0.5 * aa_synth.uniform(7, n)
+    src = aa_synth.uniform(8, n) if with_src else None
+    ud = dev(u)
+    sd = dev(src) if with_src else None
+    gd = torch.empty_like(ud)
+    P = aa.Bratu2D(s, 5.0, sd.data_ptr() if with_src else None)
+    rc = aa.builtin_g("aa_g_bratu2d")(ud.data_ptr(), gd.data_ptr(), n,
+                                        torch.cuda.current_stream().cuda_stream,
+                                        aa.C.cast(aa.C.pointer(P), aa.C.c_void_p))
+    assert rc == 0
+    ref = ora.g_bratu2d(s, 5.0, src, u)
+    assert np.max(np.abs(gd.cpu().numpy() - ref)) <= 1e-14 * (np.abs(ref).max() + 1.0)
+
+
+def test_builtin_map_rejects_wrong_size(aa):
+    b = torch.zeros(12, dtype=torch.float64, device="cuda")
+    P = aa.Jacobi3D(2, 2, 3, 0.1, 0.01, 0.8, b.data_ptr())
+    rc = aa.builtin_g("aa_g_jacobi3d")(b.data_ptr(), b.data_ptr(), 13,
+                                         torch.cuda.current_stream().cuda_stream,
+                                         aa.C.cast(aa.C.pointer(P), aa.C.c_void_p))
+    assert rc == -1  # AA_EINVAL
