@@ -65,6 +65,7 @@ struct aa_ctx {
   DevStatus *hstat;         // pinned
   double *hvec;             // pinned, MMAX doubles
   int c, head;
+  int pend_k, pend_head;    // aa_step: the add in flight between launch and finish
   int64_t it;
   aa_stats stats;
   cudaEvent_t ev[4];
@@ -435,9 +436,15 @@ static int pass_update(aa_ctx *c, const double *g, const double *x, double *xn, 
   return run(c, a);
 }
 
-static int read_status(aa_ctx *c) {
+// The status word is read in two halves so that a caller can enqueue more
+// work (a timing event) between the copy and the wait.
+static int status_copy(aa_ctx *c) {
   CUDA_TRY(cudaMemcpyAsync(c->hstat, &c->st->st, sizeof(DevStatus), cudaMemcpyDeviceToHost,
                            c->stream));
+  return AA_OK;
+}
+
+static int status_wait(aa_ctx *c) {
   CUDA_TRY(cudaStreamSynchronize(c->stream));
   if (c->tn) fold_timing(c);
   if (c->hstat->status != 0) {
@@ -449,6 +456,11 @@ static int read_status(aa_ctx *c) {
     return fail(code, "device reported %s", aa_strerror(code));
   }
   return AA_OK;
+}
+
+static int read_status(aa_ctx *c) {
+  int rc = status_copy(c);
+  return rc ? rc : status_wait(c);
 }
 
 // The QR update of Algorithm 2 for one new column (step or unit mode).
@@ -490,7 +502,11 @@ static int qr_update(aa_ctx *c, bool step, const double *x, const double *g, con
   return AA_OK;
 }
 
-extern "C" int aa_step(aa_ctx *c, const double *x, const double *g, double *xn, double *fnorm) {
+// aa_step in two halves: step_launch enqueues the passes of one iteration
+// and the copy of the status word; step_finish waits for them and updates the
+// host-side history bookkeeping.  (aa_solve records a timing event between
+// the two, so that it needs no second synchronisation.)
+static int step_launch(aa_ctx *c, const double *x, const double *g, double *xn) {
   if (!c || !x || !g || !xn) return fail(AA_EINVAL, "NULL argument");
   if (!aligned16(x) || !aligned16(g) || !aligned16(xn))
     return fail(AA_EINVAL, "device vectors must be 16-byte aligned");
@@ -508,30 +524,41 @@ extern "C" int aa_step(aa_ctx *c, const double *x, const double *g, double *xn, 
     a.out_x = xn;
     add_dot(a, 0, 0);
     if ((rc = run(c, a))) return rc;
-    if ((rc = read_status(c))) return rc;
-    c->it = 1;
-    c->stats.steps++;
-    c->stats.fnorm = sqrt(c->hstat->fnorm2);
-    if (fnorm) *fnorm = c->stats.fnorm;
-    return AA_OK;
+    return status_copy(c);
   }
   int k, head_new, dg_slot;
   if ((rc = qr_update(c, true, x, g, nullptr, &k, &head_new, &dg_slot))) return rc;
   if ((rc = pass_update(c, c->gprev, x, xn, k + 1, head_new))) return rc;
-  if ((rc = read_status(c))) return rc;
+  c->pend_k = k;
+  c->pend_head = head_new;
+  return status_copy(c);
+}
+
+static int step_finish(aa_ctx *c, double *fnorm) {
+  int rc;
+  if ((rc = status_wait(c))) return rc;
   c->stats.steps++;
   c->stats.fnorm = sqrt(c->hstat->fnorm2);
   if (fnorm) *fnorm = c->stats.fnorm;
+  if (c->it == 0) {
+    c->it = 1;
+    return AA_OK;
+  }
   if (c->hstat->breakdown) {
     c->stats.breakdowns++;
     c->c = 0;
     c->head = 0;
   } else {
-    c->c = k + 1;
-    c->head = head_new;
+    c->c = c->pend_k + 1;
+    c->head = c->pend_head;
   }
   c->it++;
   return AA_OK;
+}
+
+extern "C" int aa_step(aa_ctx *c, const double *x, const double *g, double *xn, double *fnorm) {
+  int rc = step_launch(c, x, g, xn);
+  return rc ? rc : step_finish(c, fnorm);
 }
 
 extern "C" int aa_qradd(aa_ctx *c, const double *v) {
@@ -657,9 +684,10 @@ extern "C" int aa_solve(aa_ctx *c, aa_g_fn G, void *user, double *x, aa_stats *s
     cudaEventRecord(c->ev[1], c->stream);
     double *nxt = c->xbuf[nb];
     double fn = 0;
-    rc = aa_step(c, cur, c->gbuf, nxt, &fn);
+    rc = step_launch(c, cur, c->gbuf, nxt);
     cudaEventRecord(c->ev[2], c->stream);
-    cudaEventSynchronize(c->ev[2]);
+    if (rc == AA_OK) rc = step_finish(c, &fn);  // its wait covers the event too
+    else cudaEventSynchronize(c->ev[2]);
     float t1 = 0, t2 = 0;
     cudaEventElapsedTime(&t1, c->ev[0], c->ev[1]);
     cudaEventElapsedTime(&t2, c->ev[1], c->ev[2]);
