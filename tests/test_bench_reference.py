@@ -1,0 +1,45 @@
+"""bench.py --impl reference (the CPU oracle's arm) keeps the bench line's
+contract on a small workload: one JSON line with the same metric, unit and
+direction as the GPU arm, the oracle described in cpu_baseline, an e2e object
+with no host-device traffic, and nothing printed by ranks other than 0."""
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+ARGS = ["--impl", "reference", "--nx", "40", "--ny", "40", "--nz", "40", "--m", "5",
+        "--steps", "2", "--warmup", "1"]
+
+
+def run(env_extra=None):
+    env = dict(os.environ)
+    env.update(env_extra or {})
+    return subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), *ARGS], cwd=ROOT,
+                          env=env, capture_output=True, text=True, timeout=300)
+
+
+def test_reference_line():
+    p = run({"RANK": "0", "WORLD_SIZE": "1"})
+    assert p.returncode == 0, p.stderr
+    lines = [ln for ln in p.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference"
+    assert d["metric"].startswith("AA iterations/s") and "m=5" in d["metric"]
+    assert d["unit"] == "iter/s" and d["higher_is_better"] is True
+    assert d["steps"] == 2 and d["warmup"] == 1 and d["n_gpus"] == 1
+    assert d["value"] > 0 and abs(d["ms_per_step"] - 1e3 / d["value"]) <= 1e-3 * d["ms_per_step"] + 1e-3
+    assert d["config"]["n"] == 40 * 40 * 40 and d["config"]["orth"] == "icwy"
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == d["value"]
+    assert "40x40x8 slab" in cb["sample"]
+    e2e = d["e2e"]
+    assert e2e["value"] == d["value"] and e2e["unit"] == "iter/s"
+    assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+
+
+def test_other_ranks_print_nothing():
+    p = run({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
+    assert p.returncode == 0, p.stderr
+    assert not [ln for ln in p.stdout.splitlines() if ln.startswith("{")]
