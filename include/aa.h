@@ -22,6 +22,9 @@
  *    when max_iters is reached, a negative AA_E* code on error.  No C++
  *    exception crosses the ABI.  aa_last_error() gives a message.
  *  - A context is not thread-safe; distinct contexts are independent.
+ *  - After a call returns an error that the device reported (AA_ETIMEOUT,
+ *    AA_ENONFINITE) the history is undefined: aa_step, aa_qradd and aa_lsq
+ *    return AA_ESTATE until aa_reset (aa_solve resets by itself).
  *  - The caller owns x, G(x), f and user data; the context owns the history
  *    (Q, R, T, dG, f_{i-1}, G(x_{i-1})) and its reduction scratch.
  */
@@ -122,8 +125,16 @@ int aa_create(const aa_config *cfg, aa_ctx **out);
 /* Destroy a context (synchronizes its stream, frees all device memory).  NULL is ignored. */
 void aa_destroy(aa_ctx *ctx);
 
-/* Forget the history (Algorithm 1 restarts at iteration 0). */
+/* Forget the history (Algorithm 1 restarts at iteration 0); also clears the
+ * reset-required state left by a device-reported error. */
 int aa_reset(aa_ctx *ctx);
+
+/* Test hook (no counterpart in the paper): writes `code` (0 or a negative
+ * AA_E* value) into the context's device status word on its stream, as a
+ * pass that failed on the device would, so that host-side error handling
+ * can be exercised without a device fault.  The next call that reads the
+ * status (aa_step, aa_qradd, aa_lsq) returns it.  Synchronizes. */
+int aa_test_set_device_status(aa_ctx *ctx, int code);
 
 /* Replace the stream used by later calls. */
 int aa_set_stream(aa_ctx *ctx, void *stream);
@@ -178,7 +189,8 @@ int aa_pass_times(const aa_ctx *ctx, double *ms_out, int64_t *count_out);
  * for the k columns A_j = A_dev + j*lda and nv vectors V_v = V_dev + v*ldv
  * (all FP64, columns 16-byte aligned, k*nv <= 256, lda, ldv >= n).  The
  * result is bit-identical from run to run.  Allocates its reduction scratch
- * (grid x k*nv doubles) with cudaMalloc on every call.  Synchronizes. */
+ * (grid x k*nv doubles) with cudaMalloc on every call.  Synchronizes.
+ * Returns AA_ETIMEOUT (and NaN products) if a bounded device wait ran out. */
 int aa_mdot(const double *A_dev, int64_t lda, int k, const double *V_dev, int64_t ldv, int nv,
             int64_t n, double *out_host, void *stream);
 
@@ -195,10 +207,14 @@ int aa_mdot(const double *A_dev, int64_t lda, int k, const double *V_dev, int64_
  *  - Sizes: same limits as aa_mdot (k*nv <= 256, k + nv <= 70, lda, ldv >= n,
  *    columns 16-byte aligned); larger requests return AA_EINVAL.
  *  - Output: out_dev (device, k*nv FP64, out_dev[j*nv + v]) is written on
- *    `stream`; the call does not synchronize.
+ *    `stream`; the call does not synchronize.  Since it returns before the
+ *    kernel ends, a bounded device wait that ran out cannot be returned as
+ *    a status: it shows as NaN in every product.
  *  - The first call on a device looks up the array's device address
  *    (cudaGetSymbolAddress, with that device current); make that first call
- *    before any stream capture.
+ *    before any stream capture.  The address is cached per device and
+ *    looked up again when the device's current context has changed (after
+ *    cudaDeviceReset, for example).
  *  - Every call shares the one array and leaves its contents behind; the
  *    call clears what must start at zero itself.  Calls whose work overlaps
  *    on the GPU (for example on two streams) race on the array: serialize

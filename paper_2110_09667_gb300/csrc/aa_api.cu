@@ -67,6 +67,7 @@ struct aa_ctx {
   int c, head;
   int pend_k, pend_head;    // aa_step: the add in flight between launch and finish
   int64_t it;
+  int need_reset;           // a device-reported error left the history undefined
   aa_stats stats;
   cudaEvent_t ev[4];
   // AA_FLAG_TIMING: event pairs around each pass, folded into per-kind sums
@@ -208,6 +209,26 @@ extern "C" int aa_reset(aa_ctx *c) {
   memset(c->pass_n, 0, sizeof c->pass_n);
   c->tn = 0;
   CUDA_TRY(cudaMemsetAsync(c->st, 0, sizeof(DevState), c->stream));
+  c->need_reset = 0;
+  return AA_OK;
+}
+
+// Calls that use the history refuse to run after a device-reported error
+// (a pass that gave up on a bounded wait may have rotated part of Q; a
+// non-finite residual cleared the history on the device but not on the
+// host) until aa_reset starts a fresh history.
+static int check_usable(aa_ctx *c) {
+  if (c->need_reset)
+    return fail(AA_ESTATE, "a device error left the history undefined: call aa_reset first");
+  return AA_OK;
+}
+
+extern "C" int aa_test_set_device_status(aa_ctx *c, int code) {
+  if (!c) return fail(AA_EINVAL, "NULL ctx");
+  if (code > 0) return fail(AA_EINVAL, "status codes are 0 or negative");
+  const int32_t v = code;
+  CUDA_TRY(cudaMemcpyAsync(&c->st->st.status, &v, sizeof v, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
   return AA_OK;
 }
 
@@ -453,7 +474,8 @@ static int status_wait(aa_ctx *c) {
     cudaMemsetAsync(&c->st->st.status, 0, sizeof(int32_t), c->stream);
     cudaMemsetAsync(&c->st->ticket, 0, sizeof(uint32_t), c->stream);
     cudaStreamSynchronize(c->stream);
-    return fail(code, "device reported %s", aa_strerror(code));
+    c->need_reset = 1;
+    return fail(code, "device reported %s (history undefined until aa_reset)", aa_strerror(code));
   }
   return AA_OK;
 }
@@ -511,7 +533,8 @@ static int step_launch(aa_ctx *c, const double *x, const double *g, double *xn) 
   if (!aligned16(x) || !aligned16(g) || !aligned16(xn))
     return fail(AA_EINVAL, "device vectors must be 16-byte aligned");
   if (xn == x || xn == g) return fail(AA_EINVAL, "xnext must not alias x or G(x)");
-  int rc;
+  int rc = check_usable(c);
+  if (rc) return rc;
   if (c->it == 0) {
     PassArgs a;
     base_args(c, a, K_INIT);
@@ -564,6 +587,7 @@ extern "C" int aa_step(aa_ctx *c, const double *x, const double *g, double *xn, 
 extern "C" int aa_qradd(aa_ctx *c, const double *v) {
   if (!c || !v) return fail(AA_EINVAL, "NULL argument");
   if (!aligned16(v)) return fail(AA_EINVAL, "v must be 16-byte aligned");
+  if (check_usable(c)) return AA_ESTATE;
   int k, head_new, dg_slot;
   int rc = qr_update(c, false, nullptr, nullptr, v, &k, &head_new, &dg_slot);
   if (rc) return rc;
@@ -582,6 +606,7 @@ extern "C" int aa_qradd(aa_ctx *c, const double *v) {
 extern "C" int aa_lsq(aa_ctx *c, const double *f, double *gamma_host) {
   if (!c || !f || !gamma_host) return fail(AA_EINVAL, "NULL argument");
   if (!aligned16(f)) return fail(AA_EINVAL, "f must be 16-byte aligned");
+  if (check_usable(c)) return AA_ESTATE;
   if (c->c == 0) return 0;
   PassArgs a;
   base_args(c, a, K_LSQ);
@@ -769,8 +794,12 @@ extern "C" int aa_mdot(const double *A, int64_t lda, int k, const double *V, int
   cudaError_t e = cudaMemsetAsync(st, 0, sizeof(DevState), s);
   if (e == cudaSuccess) e = launch_pass(a, 0, nsm, &grid, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(out_host, res, sizeof(double) * k * nv, cudaMemcpyDeviceToHost, s);
+  int32_t dev_status = 0;
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&dev_status, &st->st.status, sizeof dev_status, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) rc = fail(AA_ECUDA, "aa_mdot: %s", cudaGetErrorString(e));
+  else if (dev_status != 0) rc = fail(dev_status, "aa_mdot: device reported %s", aa_strerror(dev_status));
   cudaFree(st);
   cudaFree(partials);
   cudaFree(res);

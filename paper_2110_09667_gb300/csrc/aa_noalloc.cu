@@ -34,23 +34,52 @@ constexpr size_t NA_BYTES = NA_STATE_BYTES + NA_PARTIAL_BYTES;
 
 static __device__ __align__(256) unsigned char g_mdot_scratch[NA_BYTES];
 
-// Device address of g_mdot_scratch for each device, looked up once with that
+// Device address of g_mdot_scratch for each device, looked up with that
 // device current (in host code the symbol name is only a host-side stand-in).
+// The address belongs to the context the module was loaded into, so the
+// cache is keyed on the current context as well: after cudaDeviceReset (a new
+// primary context) the address is looked up again instead of reusing a
+// pointer into the destroyed context.
 constexpr int NA_MAX_DEVICES = 64;
 std::mutex g_na_mutex;
 void *g_na_ptr[NA_MAX_DEVICES];
+void *g_na_ctx[NA_MAX_DEVICES];
+
+typedef int (*ctx_get_current_fn)(void **);  // cuCtxGetCurrent(CUcontext *)
+
+void *current_context() {
+  static ctx_get_current_fn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (ctx_get_current_fn)p;
+    cudaGetLastError();
+    tried = true;
+  }
+  void *ctx = nullptr;
+  if (fn && fn(&ctx) != 0) ctx = nullptr;
+  return ctx;
+}
 
 int scratch_for_current_device(void **out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NA_MAX_DEVICES) return AA_ECUDA;
   std::lock_guard<std::mutex> lock(g_na_mutex);
-  if (!g_na_ptr[dev]) {
+  // (A thread whose runtime has not bound a context yet reads NULL here; the
+  // look-up below binds it, and the context is read again after it.)
+  void *ctx = current_context();
+  if (!g_na_ptr[dev] || ctx != g_na_ctx[dev]) {
     void *p = nullptr;
     if (cudaGetSymbolAddress(&p, g_mdot_scratch) != cudaSuccess || !p) {
       cudaGetLastError();
       return AA_ECUDA;
     }
     g_na_ptr[dev] = p;
+    g_na_ctx[dev] = current_context();
   }
   *out = g_na_ptr[dev];
   return AA_OK;

@@ -1229,20 +1229,27 @@ __global__ void __launch_bounds__(NT) pass_kernel(const __grid_constant__ PassAr
     }
   }
 
+  const bool has_epilogue = a.ndots > 0 || a.kind == K_A || a.kind == K_PROJ;
   if (s_err) {
-    // A copy did not complete in time: record it, give the copies still in
-    // flight a bounded chance to land, and leave without touching the state.
+    // A copy did not complete in time: record it and give the copies still
+    // in flight a bounded chance to land.  This CTA's partial sums are
+    // unknown, so it posts NaN for every dot product and still takes its
+    // ticket: the last CTA then finishes the reduction (NaN results), leaves
+    // the m x m state untouched and resets the ticket for the next launch.
     if (tid == 0) {
       atomicExch(&S->st.status, DEV_ETIMEOUT);
       for (int s = 0; s < nstages; ++s) (void)mbar_wait_bounded(&bars[s], 0);
     }
-    return;
+    if (!has_epilogue) return;
+    for (int d = tid; d < a.ndots; d += NT)
+      a.partials[(size_t)blockIdx.x * NDOT_MAX + d] = __longlong_as_double(0x7ff8000000000000LL);
   }
-  const bool has_epilogue = a.ndots > 0 || a.kind == K_A || a.kind == K_PROJ;
   if (!has_epilogue) return;
 
   // Per-CTA partial sums (warp butterfly, then warps in order: fixed order).
-  if (rowdots || MODE == 1) {
+  if (s_err) {
+    // (NaN partials posted above)
+  } else if (rowdots || MODE == 1) {
     const int nrow = (MODE == 1) ? dbase : a.ndots;
     __shared__ double rdw[NWARP][RD];
 #pragma unroll
@@ -1259,7 +1266,7 @@ __global__ void __launch_bounds__(NT) pass_kernel(const __grid_constant__ PassAr
       a.partials[(size_t)blockIdx.x * NDOT_MAX + tid] = v;
     }
   }
-  if (!rowdots) {
+  if (!rowdots && !s_err) {
 #pragma unroll
     for (int i = 0; i < DPW; ++i) {
       const int d = dbase + warp + NWARP * i;
@@ -1293,7 +1300,11 @@ __global__ void __launch_bounds__(NT) pass_kernel(const __grid_constant__ PassAr
   __threadfence();
   __syncthreads();
   if (warp == 0) {
-    epilogue(a, (double *)smem, lane);
+    // After a timed-out copy anywhere in the grid the sums are NaN: a plain
+    // multi-dot still publishes them (NaN marks the failure for callers that
+    // cannot read the status word); the m x m state is left as it was.
+    const bool timed_out = *(volatile int32_t *)&S->st.status == DEV_ETIMEOUT;
+    if (!timed_out || a.kind == K_MDOT) epilogue(a, (double *)smem, lane);
     if (lane == 0) S->ticket = 0;
     __threadfence();
   }

@@ -46,3 +46,23 @@ def test_noalloc_rejects_oversize():
     out = torch.empty(400, dtype=torch.float64, device="cuda")
     with pytest.raises(aa.AAError):
         aa.mdot_noalloc(A, V, out)
+
+
+def test_noalloc_leaves_free_memory_unchanged():
+    """The property the entry point exists for: after a first call (which
+    looks up the scratch array's address and loads the kernel), further
+    calls change the device's free memory by nothing."""
+    import paper_2110_09667_gb300 as aa
+    n = (1 << 18) + 5
+    A, V = padded(4, n, 7), padded(3, n, 8)
+    out = torch.empty(12, dtype=torch.float64, device="cuda")
+    aa.mdot_noalloc(A, V, out)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(5):
+        aa.mdot_noalloc(A, V, out)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
+    ref = aa.mdot(A, V)
+    assert np.allclose(out.cpu().numpy().reshape(4, 3), ref, rtol=1e-13, atol=0)
