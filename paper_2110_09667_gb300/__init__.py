@@ -119,6 +119,53 @@ def _ptr(t) -> C.c_void_p:
     return C.c_void_p(t.data_ptr())
 
 
+# The C ABI sees only pointers and sizes, so every tensor is checked here
+# before its pointer is passed: a wrong dtype, a strided view or a short
+# buffer would otherwise make a kernel read or write past its end.  Shapes
+# and strides are checked first, then the dtype, then the device.
+
+def _check_dtype_device(*named):
+    """(tensor, name) pairs: every dtype first, then every device."""
+    import torch
+    for t, name in named:
+        if t.dtype != torch.float64:
+            raise ValueError(f"{name}: expected a float64 tensor, got {t.dtype}")
+    for t, name in named:
+        if not t.is_cuda:
+            raise ValueError(f"{name}: expected a CUDA tensor, got device {t.device}")
+
+
+def _vec(t, n: int, name: str, dev: bool = True):
+    """A float64 CUDA vector holding at least n contiguous values."""
+    if t.dim() != 1:
+        raise ValueError(f"{name}: expected a 1-D tensor, got shape {tuple(t.shape)}")
+    if t.numel() < n:
+        raise ValueError(f"{name}: expected at least {n} elements, got {t.numel()}")
+    if t.numel() > 1 and t.stride(0) != 1:
+        raise ValueError(f"{name}: expected unit stride, got {t.stride(0)}")
+    if dev:
+        _check_dtype_device((t, name))
+    return _ptr(t)
+
+
+def _cols(t, name: str, n: int | None = None, dev: bool = True):
+    """A float64 CUDA matrix whose rows are the columns of the ABI call."""
+    if t.dim() != 2:
+        raise ValueError(f"{name}: expected a 2-D tensor (columns x n), got shape {tuple(t.shape)}")
+    rows, cols = t.shape
+    if rows < 1 or cols < 1:
+        raise ValueError(f"{name}: empty shape {tuple(t.shape)}")
+    if n is not None and cols != n:
+        raise ValueError(f"{name}: expected {n} entries per column, got {cols}")
+    if cols > 1 and t.stride(1) != 1:
+        raise ValueError(f"{name}: entries of a column must be contiguous (stride(1) == 1)")
+    if rows > 1 and t.stride(0) < cols:
+        raise ValueError(f"{name}: column stride {t.stride(0)} is shorter than n = {cols}")
+    if dev:
+        _check_dtype_device((t, name))
+    return _ptr(t)
+
+
 def builtin_g(name: str):
     """C function pointer of a built-in map (aa_g_jacobi2d/3d, aa_g_bratu2d)."""
     return GFN(C.cast(getattr(lib(), name), C.c_void_p).value)
@@ -163,26 +210,35 @@ class Anderson:
         _check(lib().aa_reset(self._h))
 
     def qradd(self, v) -> int:
-        return _check(lib().aa_qradd(self._h, _ptr(v)), allow=(AA_OK, AA_EBREAKDOWN))
+        return _check(lib().aa_qradd(self._h, _vec(v, self.n, "v")), allow=(AA_OK, AA_EBREAKDOWN))
 
     def lsq(self, f):
         import numpy as np
         g = (C.c_double * max(self.m, 1))()
-        k = _check(lib().aa_lsq(self._h, _ptr(f), g), allow=tuple(range(0, self.m + 1)))
+        k = _check(lib().aa_lsq(self._h, _vec(f, self.n, "f"), g), allow=tuple(range(0, self.m + 1)))
         return np.array(g[:k])
 
     def step(self, x, gx, xnext) -> float:
         fn = C.c_double(0.0)
-        _check(lib().aa_step(self._h, _ptr(x), _ptr(gx), _ptr(xnext), C.byref(fn)))
+        _check(lib().aa_step(self._h, _vec(x, self.n, "x"), _vec(gx, self.n, "gx"),
+                             _vec(xnext, self.n, "xnext"), C.byref(fn)))
         return fn.value
 
     def solve(self, gfn, user, x):
         """aa_solve with a C function pointer (builtin_g) and its parameter struct."""
         st = Stats()
+        xp = _vec(x, self.n, "x")
         rc = lib().aa_solve(self._h, gfn, C.cast(C.pointer(user), C.c_void_p) if user is not None
-                            else None, _ptr(x), C.byref(st))
+                            else None, xp, C.byref(st))
         _check(rc, allow=(AA_OK, AA_NOTCONVERGED))
         return rc, st.as_dict()
+
+    def test_set_device_status(self, code: int):
+        """aa_test_set_device_status: plant a device status word (host-side
+        fault injection for the error-handling tests)."""
+        L = lib()
+        L.aa_test_set_device_status.argtypes = [C.c_void_p, C.c_int]
+        _check(L.aa_test_set_device_status(self._h, int(code)))
 
     def get_qr(self):
         import numpy as np
@@ -213,20 +269,26 @@ class Anderson:
 def mdot(A, V):
     """A^T V for FP64 CUDA tensors A (k x n, rows are columns) and V (nv x n)."""
     import numpy as np
+    pa = _cols(A, "A", dev=False)
     k, n = A.shape
+    pv = _cols(V, "V", n, dev=False)
     nv = V.shape[0]
+    _check_dtype_device((A, "A"), (V, "V"))
     out = np.zeros(k * nv)
-    _check(lib().aa_mdot(_ptr(A), A.stride(0), k, _ptr(V), V.stride(0), nv, n,
+    _check(lib().aa_mdot(pa, A.stride(0), k, pv, V.stride(0), nv, n,
                          out.ctypes.data_as(_dp), _stream()))
     return out.reshape(k, nv)
 
 
 def mdot_noalloc(A, V, out):
     """aa_mdot_noalloc: A^T V into the FP64 CUDA tensor out (k*nv), no allocation."""
+    pa = _cols(A, "A", dev=False)
     k, n = A.shape
+    pv = _cols(V, "V", n, dev=False)
     nv = V.shape[0]
-    rc = lib().aa_mdot_noalloc(_ptr(A), A.stride(0), k, _ptr(V), V.stride(0), nv, n, _ptr(out),
-                               _stream())
+    po = _vec(out, k * nv, "out", dev=False)
+    _check_dtype_device((A, "A"), (V, "V"), (out, "out"))
+    rc = lib().aa_mdot_noalloc(pa, A.stride(0), k, pv, V.stride(0), nv, n, po, _stream())
     if rc != AA_OK:
         raise AAError(rc, "aa_mdot_noalloc failed")
     return out
@@ -342,8 +404,9 @@ class Batch:
 
 def exp_fp32pipe(u):
     """e^u on the FP32 pipe (aa_exp_fp32pipe) for an FP64 CUDA tensor."""
+    pu = _vec(u, u.numel(), "u")
     out = u.new_empty(u.shape)
-    _check(_batch_lib().aa_exp_fp32pipe(u.numel(), _ptr(u), _ptr(out), _stream()))
+    _check(_batch_lib().aa_exp_fp32pipe(u.numel(), pu, _ptr(out), _stream()))
     return out
 
 
