@@ -30,8 +30,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "aa_oracle.c")
 _LIB_DIR = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_LIB_DIR, "liboracle.so")
+_LIB_OMP = os.path.join(_LIB_DIR, "liboracle_omp.so")
 _lock = threading.Lock()
-_lib = None
+_libs = {}
 
 MGS, ICWY, CGS2, DCGS2 = 0, 1, 2, 3
 ORTH = {"mgs": MGS, "icwy": ICWY, "cgs2": CGS2, "dcgs2": DCGS2}
@@ -47,24 +48,34 @@ class _Problem(C.Structure):
                 ("b", _dp), ("fn", GFN), ("user", C.c_void_p)]
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc into oracle/_build/liboracle.so."""
+def build(force: bool = False, omp: bool = False) -> str:
+    """Compile the oracle with gcc: oracle/_build/liboracle.so, the reference
+    build (sequential loops and sums), or with omp=True liboracle_omp.so, the
+    timed build (the same source with -fopenmp: parallel element-wise loops,
+    fixed-chunk dot products combined in chunk order)."""
+    out = _LIB_OMP if omp else _LIB
     with _lock:
-        if (not force and os.path.exists(_LIB)
-                and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
-            return _LIB
+        if (not force and os.path.exists(out)
+                and os.path.getmtime(out) >= os.path.getmtime(_SRC)):
+            return out
         os.makedirs(_LIB_DIR, exist_ok=True)
-        tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared",
+        tmp = out + f".tmp{os.getpid()}"
+        flags = ["-fopenmp"] if omp else []
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", *flags,
                                "-ffp-contract=off", "-fno-fast-math", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
-        return _LIB
+        os.replace(tmp, out)
+        return out
 
 
-def lib():
-    global _lib
-    if _lib is None:
-        L = C.CDLL(build())
+def set_threads(nthreads: int) -> int:
+    """Threads of the timed (OpenMP) build; returns the count in effect."""
+    return int(lib(omp=True).ora_set_threads(int(nthreads)))
+
+
+def lib(omp: bool = False):
+    L = _libs.get(omp)
+    if L is None:
+        L = C.CDLL(build(omp=omp))
         L.ora_create.restype = C.c_void_p
         L.ora_create.argtypes = [C.c_int64, C.c_int, C.c_int]
         L.ora_destroy.argtypes = [C.c_void_p]
@@ -81,10 +92,13 @@ def lib():
         L.ora_g_jacobi3d.argtypes = [C.c_int64, C.c_int64, C.c_int64, C.c_double, C.c_double,
                                      C.c_double, _dp, _dp, _dp]
         L.ora_g_bratu2d.argtypes = [C.c_int64, C.c_double, _dp, _dp, _dp]
+        L.ora_store_round.restype = C.c_double
+        L.ora_store_round.argtypes = [C.c_int, C.c_double]
         L.ora_solve.argtypes = [C.c_void_p, C.POINTER(_Problem), _dp, C.c_int, C.c_double,
                                 C.c_double, C.c_int, C.c_int, _dp, _dp, C.POINTER(C.c_int)]
-        _lib = L
-    return _lib
+        L.ora_set_threads.argtypes = [C.c_int]
+        _libs[omp] = L
+    return L
 
 
 def _p(a: np.ndarray | None):
@@ -99,10 +113,10 @@ class Oracle:
 
     def __init__(self, n: int, m: int, orth="mgs", *, dcgs2_min_mi: int = 3,
                  dcgs2_scaled: bool = False, store_round: int = 0,
-                 breakdown_tol: float = 1e-14):
+                 breakdown_tol: float = 1e-14, omp: bool = False):
         self.n, self.m = int(n), int(m)
         self.orth = ORTH[orth] if isinstance(orth, str) else int(orth)
-        L = lib()
+        self._L = L = lib(omp)
         self._h = L.ora_create(self.n, self.m, self.orth)
         if not self._h:
             raise MemoryError("ora_create failed")
@@ -112,31 +126,31 @@ class Oracle:
         L.ora_set_option(self._h, 3, float(breakdown_tol))
 
     def close(self):
-        if self._h:
-            lib().ora_destroy(self._h)
+        if getattr(self, "_h", None):
+            self._L.ora_destroy(self._h)
             self._h = None
 
     __del__ = close
 
     def reset(self):
-        lib().ora_reset(self._h)
+        self._L.ora_reset(self._h)
 
     def counters(self) -> dict:
         out = (C.c_longlong * 4)()
-        lib().ora_counters(self._h, out)
+        self._L.ora_counters(self._h, out)
         return {"syncs_qr": out[0], "syncs_lsq": out[1], "syncs_other": out[2], "cols": out[3]}
 
     def qradd(self, v: np.ndarray) -> int:
         v = np.ascontiguousarray(v, dtype=np.float64)
-        return lib().ora_qradd(self._h, _p(v))
+        return self._L.ora_qradd(self._h, _p(v))
 
     def qrdelete(self) -> int:
-        return lib().ora_qrdelete(self._h)
+        return self._L.ora_qrdelete(self._h)
 
     def lsq(self, f: np.ndarray) -> np.ndarray:
         f = np.ascontiguousarray(f, dtype=np.float64)
         g = np.zeros(self.m, dtype=np.float64)
-        k = lib().ora_lsq(self._h, _p(f), _p(g))
+        k = self._L.ora_lsq(self._h, _p(f), _p(g))
         return g[:k].copy()
 
     def get_qr(self):
@@ -145,7 +159,7 @@ class Oracle:
         R = np.zeros((self.m, self.m), dtype=np.float64)
         T = np.zeros((self.m, self.m), dtype=np.float64)
         k = C.c_int(0)
-        lib().ora_get_qr(self._h, _p(Q), _p(R), _p(T), C.byref(k))
+        self._L.ora_get_qr(self._h, _p(Q), _p(R), _p(T), C.byref(k))
         k = k.value
         return Q[:k].T.copy(), R[:k, :k].copy(), T[:k, :k].copy()
 
@@ -158,7 +172,7 @@ class Oracle:
         if T is not None:
             Tf = np.zeros((self.m, self.m))
             Tf[:k, :k] = T
-        lib().ora_set_qr(self._h, _p(Qc), _p(Rf), _p(Tf), k)
+        self._L.ora_set_qr(self._h, _p(Qc), _p(Rf), _p(Tf), k)
 
     def step(self, x: np.ndarray, g: np.ndarray):
         """One AA iteration; returns (x_next, ||f_i||, status)."""
@@ -166,7 +180,7 @@ class Oracle:
         g = np.ascontiguousarray(g, dtype=np.float64)
         xn = np.empty(self.n)
         fn = C.c_double(0.0)
-        st = lib().ora_step(self._h, _p(x), _p(g), _p(xn), C.byref(fn))
+        st = self._L.ora_step(self._h, _p(x), _p(g), _p(xn), C.byref(fn))
         return xn, fn.value, st
 
     def solve(self, problem: dict, x0: np.ndarray, *, max_iters: int, tol: float,
@@ -177,7 +191,7 @@ class Oracle:
         resid = np.zeros(max_iters + 2)
         rec = np.zeros((max(nrec, 1), self.n))
         it = C.c_int(0)
-        st = lib().ora_solve(self._h, C.byref(P), _p(x), int(max_iters), float(tol),
+        st = self._L.ora_solve(self._h, C.byref(P), _p(x), int(max_iters), float(tol),
                              float(scale), int(stop_kind), int(nrec), _p(rec), _p(resid),
                              C.byref(it))
         del keep
@@ -225,6 +239,11 @@ def make_problem(problem: dict):
     return P, keep
 
 
+def store_round(mode: int, x: float) -> float:
+    """One stored history entry: mode 0 FP64, 1 FP32, 2 BF16 (via FP32)."""
+    return lib().ora_store_round(int(mode), float(x))
+
+
 def g_jacobi2d(nx, ny, eps, b, x):
     gx = np.empty(nx * ny)
     lib().ora_g_jacobi2d(nx, ny, eps, _p(np.ascontiguousarray(b, dtype=np.float64)),
@@ -232,9 +251,9 @@ def g_jacobi2d(nx, ny, eps, b, x):
     return gx
 
 
-def g_jacobi3d(nx, ny, nz, ey, ez, omega, b, x):
+def g_jacobi3d(nx, ny, nz, ey, ez, omega, b, x, omp: bool = False):
     gx = np.empty(nx * ny * nz)
-    lib().ora_g_jacobi3d(nx, ny, nz, ey, ez, omega,
+    lib(omp).ora_g_jacobi3d(nx, ny, nz, ey, ez, omega,
                          _p(np.ascontiguousarray(b, dtype=np.float64)),
                          _p(np.ascontiguousarray(x, dtype=np.float64)), _p(gx))
     return gx

@@ -34,6 +34,22 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Two builds of this one file.  The reference build (plain gcc) runs every
+ * loop and every sum sequentially, as described above.  The timed build
+ * (gcc -fopenmp) runs the element-wise loops in parallel with static
+ * schedules, which changes no arithmetic, and each dot product as fixed
+ * contiguous chunks (one per thread) whose partial sums are added in chunk
+ * order: the same result for the same thread count, and with one thread
+ * exactly the reference build's sum. */
+#ifdef _OPENMP
+#define ORA_PAR_FOR _Pragma("omp parallel for schedule(static)")
+#else
+#define ORA_PAR_FOR
+#endif
 
 #define ORA_MGS 0
 #define ORA_ICWY 1
@@ -71,10 +87,30 @@ typedef struct ora_ctx {
 
 /* ---------------------------------------------------------------- helpers */
 
-static double dot(const double *a, const double *b, int64_t n) {
+static double dot_seq(const double *a, const double *b, int64_t n) {
   double s = 0.0;
   for (int64_t i = 0; i < n; ++i) s += a[i] * b[i];
   return s;
+}
+
+static double dot(const double *a, const double *b, int64_t n) {
+#ifdef _OPENMP
+  enum { MAXCH = 1024 };
+  int nch = omp_get_max_threads();
+  if (nch > MAXCH) nch = MAXCH;
+  if (nch > 1 && n >= 4096) {
+    double part[MAXCH];
+#pragma omp parallel for schedule(static, 1)
+    for (int ch = 0; ch < nch; ++ch) {
+      const int64_t lo = n * ch / nch, hi = n * (ch + 1) / nch;
+      part[ch] = dot_seq(a + lo, b + lo, hi - lo);
+    }
+    double s = 0.0;
+    for (int ch = 0; ch < nch; ++ch) s += part[ch];
+    return s;
+  }
+#endif
+  return dot_seq(a, b, n);
 }
 
 static double nrm2(const double *a, int64_t n) { return sqrt(dot(a, a, n)); }
@@ -96,10 +132,34 @@ static double round_bf16(double x) {
 
 static void store_round_vec(ora_ctx *c, double *a) {
   if (c->store_round == 1) {
+    ORA_PAR_FOR
     for (int64_t i = 0; i < c->n; ++i) a[i] = (double)(float)a[i];
   } else if (c->store_round == 2) {
+    ORA_PAR_FOR
     for (int64_t i = 0; i < c->n; ++i) a[i] = round_bf16(a[i]);
   }
+}
+
+/* Threads of the timed (OpenMP) build; returns the count in effect (1 in
+ * the reference build). */
+int ora_set_threads(int nthreads) {
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+  return omp_get_max_threads();
+#else
+  (void)nthreads;
+  return 1;
+#endif
+}
+
+/* One stored history entry as the precision form keeps it: mode 1 FP32
+ * (round to nearest), mode 2 BF16 (FP64 -> FP32 round to nearest, then
+ * FP32 -> BF16 round to nearest even); mode 0 leaves it FP64.  Exported so
+ * that the rounding itself can be pinned against literal bit patterns. */
+double ora_store_round(int mode, double x) {
+  if (mode == 1) return (double)(float)x;
+  if (mode == 2) return round_bf16(x);
+  return x;
 }
 
 /* ------------------------------------------------------------- lifecycle */
@@ -200,6 +260,7 @@ static void qr_delete(ora_ctx *c) {
     R[(j + 1) * M + j] = 0.0;
     double *qj = col(c->Q, n, j);
     double *qj1 = col(c->Q, n, j + 1);
+    ORA_PAR_FOR
     for (int64_t i = 0; i < n; ++i) {
       double a_i = qj[i];
       double b_i = qj1[i];
@@ -243,6 +304,7 @@ static double add_mgs(ora_ctx *c, double *v, int k) {
     double r = dot(qj, v, n);
     c->syncs_qr += 1;
     c->R[j * M + k] = r;
+    ORA_PAR_FOR
     for (int64_t i = 0; i < n; ++i) v[i] -= r * qj[i];
   }
   double rho = nrm2(v, n);
@@ -270,6 +332,7 @@ static double add_icwy(ora_ctx *c, double *v, int k) {
   for (int j = 0; j < k; ++j) {
     const double *qj = col(c->Q, n, j);
     double r = c->R[j * M + k];
+    ORA_PAR_FOR
     for (int64_t i = 0; i < n; ++i) v[i] -= r * qj[i];
   }
   double rho = nrm2(v, n);
@@ -289,6 +352,7 @@ static double add_cgs2(ora_ctx *c, double *v, int k) {
   memcpy(y, v, sizeof(double) * (size_t)n);
   for (int j = 0; j < k; ++j) {
     const double *qj = col(c->Q, n, j);
+    ORA_PAR_FOR
     for (int64_t i = 0; i < n; ++i) y[i] -= s[j] * qj[i];
   }
   for (int j = 0; j < k; ++j) z[j] = dot(col(c->Q, n, j), y, n);
@@ -296,6 +360,7 @@ static double add_cgs2(ora_ctx *c, double *v, int k) {
   memcpy(v, y, sizeof(double) * (size_t)n);
   for (int j = 0; j < k; ++j) {
     const double *qj = col(c->Q, n, j);
+    ORA_PAR_FOR
     for (int64_t i = 0; i < n; ++i) v[i] -= z[j] * qj[i];
   }
   for (int j = 0; j < k; ++j) c->R[j * M + k] = s[j] + z[j];
@@ -324,6 +389,7 @@ static double add_dcgs2(ora_ctx *c, double *v, int k) {
   if (reorth) {
     for (int j = 0; j < k - 1; ++j) {
       const double *qj = col(c->Q, n, j);
+      ORA_PAR_FOR
       for (int64_t i = 0; i < n; ++i) qprev[i] -= s[j] * qj[i];
     }
     store_round_vec(c, qprev);
@@ -334,6 +400,7 @@ static double add_dcgs2(ora_ctx *c, double *v, int k) {
   for (int j = 0; j < k; ++j) {
     const double *qj = col(c->Q, n, j);
     double r = c->R[j * M + k];
+    ORA_PAR_FOR
     for (int64_t i = 0; i < n; ++i) v[i] -= r * qj[i];
   }
   double rho = nrm2(v, n);
@@ -378,6 +445,7 @@ int ora_qradd(ora_ctx *c, const double *vin) {
   }
   c->R[k * M + k] = rho;
   double *qk = col(c->Q, n, k);
+  ORA_PAR_FOR
   for (int64_t i = 0; i < n; ++i) qk[i] = v[i] / rho;
   store_round_vec(c, qk);
   if (c->orth == ORA_ICWY) {
@@ -439,6 +507,7 @@ int ora_step(ora_ctx *c, const double *x, const double *g, double *xnext, double
   const int64_t n = c->n;
   const int M = c->m;
   double *f = c->f;
+  ORA_PAR_FOR
   for (int64_t i = 0; i < n; ++i) f[i] = g[i] - x[i];
   double fn = nrm2(f, n);
   c->syncs_other += 1;
@@ -455,6 +524,7 @@ int ora_step(ora_ctx *c, const double *x, const double *g, double *xnext, double
   double *df = c->y; /* reuse as scratch before qradd copies it */
   double *dfcopy = (double *)malloc(sizeof(double) * (size_t)n);
   if (!dfcopy) return ORA_ENOMEM;
+  ORA_PAR_FOR
   for (int64_t i = 0; i < n; ++i) dfcopy[i] = f[i] - c->f_prev[i];
   (void)df;
   int was_full = (c->c == M);
@@ -471,6 +541,7 @@ int ora_step(ora_ctx *c, const double *x, const double *g, double *xnext, double
     ng = c->c;
     int slot = (c->head + ng - 1) % M;
     double *dg = col(c->dG, n, slot);
+    ORA_PAR_FOR
     for (int64_t i = 0; i < n; ++i) dg[i] = g[i] - c->g_prev[i];
     store_round_vec(c, dg);
     double gamma[256];
@@ -479,6 +550,7 @@ int ora_step(ora_ctx *c, const double *x, const double *g, double *xnext, double
     memcpy(xnext, g, sizeof(double) * (size_t)n);
     for (int j = 0; j < ng; ++j) {
       const double *dgj = col(c->dG, n, (c->head + j) % M);
+      ORA_PAR_FOR
       for (int64_t i = 0; i < n; ++i) xnext[i] -= gamma[j] * dgj[i];
     }
   }
@@ -496,6 +568,7 @@ int ora_step(ora_ctx *c, const double *x, const double *g, double *xnext, double
 void ora_g_jacobi2d(int64_t nx, int64_t ny, double eps, const double *b, const double *x,
                     double *gx) {
   const double d = 2.0 + 2.0 * eps;
+  ORA_PAR_FOR
   for (int64_t j = 0; j < ny; ++j)
     for (int64_t i = 0; i < nx; ++i) {
       int64_t p = j * nx + i;
@@ -515,6 +588,7 @@ void ora_g_jacobi3d(int64_t nx, int64_t ny, int64_t nz, double ey, double ez, do
                     const double *b, const double *x, double *gx) {
   const double d = 2.0 * (1.0 + ey + ez);
   const int64_t sxy = nx * ny;
+  ORA_PAR_FOR
   for (int64_t k = 0; k < nz; ++k)
     for (int64_t j = 0; j < ny; ++j)
       for (int64_t i = 0; i < nx; ++i) {
@@ -536,6 +610,7 @@ void ora_g_jacobi3d(int64_t nx, int64_t ny, int64_t nz, double ey, double ez, do
 void ora_g_bratu2d(int64_t s, double lambda, const double *src, const double *u, double *gu) {
   const double h = 1.0 / (double)(s + 1);
   const double h2 = h * h;
+  ORA_PAR_FOR
   for (int64_t j = 0; j < s; ++j)
     for (int64_t i = 0; i < s; ++i) {
       int64_t p = j * s + i;

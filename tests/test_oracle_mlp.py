@@ -17,6 +17,31 @@ def params_for(dims, seed):
     return out
 
 
+# GELU(z) = z Phi(z) at points where Phi, the standard normal CDF, has
+# well-known tabulated values: Phi(1) = 0.8413447460685429,
+# Phi(2) = 0.9772498680518208, Phi(3) = 0.9986501019683699, Phi(-z) = 1 - Phi(z);
+# the density phi(1) = e^(-1/2) / sqrt(2 pi) = 0.24197072451914337.
+GELU_TABLE = [
+    (1.0, 0.8413447460685429),
+    (-1.0, -(1.0 - 0.8413447460685429)),
+    (2.0, 2.0 * 0.9772498680518208),
+    (-2.0, -2.0 * (1.0 - 0.9772498680518208)),
+    (3.0, 3.0 * 0.9986501019683699),
+    (-3.0, -3.0 * (1.0 - 0.9986501019683699)),
+]
+
+
+def test_gelu_tabulated_values():
+    for z, ref in GELU_TABLE:
+        got = mlp.gelu(np.array([z]))[0]
+        assert abs(got - ref) <= 4e-16 * max(1.0, abs(ref)), (z, got, ref)
+    # derivative Phi(z) + z phi(z): 0.5 at 0, Phi(1) + phi(1) at 1, Phi(-1) - phi(1) at -1
+    assert mlp.gelu_grad(np.array([0.0]))[0] == 0.5
+    assert abs(mlp.gelu_grad(np.array([1.0]))[0] - (0.8413447460685429 + 0.24197072451914337)) < 1e-15
+    assert abs(mlp.gelu_grad(np.array([-1.0]))[0]
+               - ((1.0 - 0.8413447460685429) - 0.24197072451914337)) < 1e-15
+
+
 def test_gelu_closed_forms():
     assert mlp.gelu(np.array([0.0]))[0] == 0.0
     assert abs(mlp.gelu(np.array([1.0]))[0] - 0.5 * (1 + math.erf(1 / math.sqrt(2)))) < 1e-16
