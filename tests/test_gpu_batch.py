@@ -177,3 +177,23 @@ def test_batch_full_size_sampled(aa, ora):
         # the kernel reports ||f|| of the returned iterate
         assert abs(res - rs[i]) <= 1e-6 * res + 1e-14, (i, res, rs[i])
         assert res >= 1e-8
+
+
+def test_batch_early_iterates_large_sides(aa, ora):
+    """Early iterates at the workload's large sides: a 256 x 256 solve streams
+    128 row blocks of 512 rows through each CTA's cp.async double buffer
+    (a 128 x 128 solve 32), so the buffer's refill and wait order is
+    compared with the oracle, not only its first blocks."""
+    sides = [256, 128, 200, 97]
+    lams = np.array([1.5, 5.0, 3.0, 6.0])
+    srcs = srcs_for(sides, 74)
+    B = aa.Batch(sides, lams, m=10, max_iters=15, src=np.concatenate(srcs))
+    B.solve(block=512)
+    it, rs, st = B.results()
+    for i, s in enumerate(sides):
+        r, _ = oracle_solve(ora, s, lams[i], srcs[i], 15)
+        assert it[i] == r["iters"], (i, it[i], r["iters"])
+        xg = B.solution(i)
+        d = xg - r["x"]
+        assert np.linalg.norm(d) <= 1e-4 * np.linalg.norm(r["x"]), (i, s)
+        assert np.max(np.abs(d)) <= 1e-4 * np.max(np.abs(r["x"])), (i, s)
