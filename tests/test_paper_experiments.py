@@ -4,7 +4,8 @@ The paper prints iteration counts (its figures are not available):
 - Heat-2D + nonlinear term 1, 1024^2, m = 5: 11 iterations for all variants
   (Sec. 5.1.1);
 - Heat-2D + nonlinear term 2, 1024^2, m = 10: 27-42 iterations depending on
-  variant and process count, CGS-2 best (Sec. 5.1.2);
+  variant and process count, CGS-2 best (Sec. 5.1.2); pinned here against a
+  backward-stable least-squares reference (see the comment above its tests);
 - Bratu, lambda = 6.7, 1024^2, m = 30: fewer than 30 iterations for all
   variants (Sec. 5.2).
 The paper's G applies A^{-1} by PCG to 1e-10; here A^{-1} is exact (DST-I),
@@ -46,11 +47,87 @@ def test_bratu_fewer_than_30(ora):
         assert r["status"] == ora.OK and r["iters"] < 30, (orth, r["iters"])
 
 
-def test_heat_term2_cgs2_converges(ora):
+# Heat-2D + nonlinear term 2 (Sec. 5.1.2), c(u) = 100 (u - u^2), m = 10: the
+# paper reports 27-42 iterations depending on the variant AND on the process
+# count, i.e. on the order of the reductions -- a sign that this run is
+# sensitive to rounding.  G is not a contraction here (c'(u) = 100 (1 - 2u)
+# against the Laplacian's smallest eigenvalue 2 pi^2: a few modes are
+# amplified about 5x), and the history becomes ill-conditioned (kappa(F) >
+# 1e7 from iteration ~30, 1e12 near the end).  With the exact inner solve used
+# here, the reference behaviour is Anderson acceleration with a backward-
+# stable least-squares solve of the full history (Householder QR, no
+# updating), which converges in 44 iterations at 1024^2.  The QR-updating
+# variants whose Q loses orthogonality (MGS, ICWY: O(eps kappa) per update,
+# accumulated across the updates; DCGS-2: its delayed reorthogonalisation,
+# which the paper calls unstable) produce a least-squares solution gamma with
+# O(1) error once kappa passes ~1e7 and diverge; CGS-2 keeps Q orthogonal to
+# O(eps) and tracks the stable reference.
+
+
+def householder_aa(G, x0, m, iters, tol):
+    """Algorithm 1 by definition with a backward-stable least-squares solve
+    (Householder QR of the explicit difference matrix, no updating).
+    Returns (iterations to ||x_{i+1} - x_i||_2 < tol, x, per-step data)."""
+    import scipy.linalg as sl
+    g0 = G(x0)
+    gs, fs, x = [g0], [g0 - x0], g0
+    steps = []
+    for i in range(1, iters + 1):
+        g = G(x)
+        f = g - x
+        gs.append(g)
+        fs.append(f)
+        mi = min(m, i)
+        dF = np.column_stack([fs[k + 1] - fs[k] for k in range(i - mi, i)])
+        dG = np.column_stack([gs[k + 1] - gs[k] for k in range(i - mi, i)])
+        Q, R = np.linalg.qr(dF)
+        gamma = sl.solve_triangular(R, Q.T @ f)
+        steps.append((fs[i] - fs[i - 1], f, gamma, dF))
+        xn = g - dG @ gamma
+        if np.linalg.norm(xn - x) < tol:
+            return i, xn, steps
+        x = xn
+    return None, x, steps
+
+
+def test_heat_term2_stable_reference_converges_in_44():
+    G, ue = heat(N, 2)
+    its, x, _ = householder_aa(G, np.zeros(N * N), 10, 60, 1e-10)
+    assert its is not None and abs(its - 44) <= 1, its
+    assert np.max(np.abs(x - ue)) < 1e-5
+
+
+def test_heat_term2_cgs2_tracks_stable_reference(ora):
     G, ue = heat(N, 2)
     r = solve(ora, G, 10, "cgs2")
-    assert r["status"] == ora.OK and r["iters"] <= 45, r["iters"]
+    assert r["status"] == ora.OK and abs(r["iters"] - 44) <= 1, r["iters"]
     assert np.max(np.abs(r["x"] - ue)) < 1e-5
+
+
+def test_heat_term2_gamma_on_a_shared_history(ora):
+    """The mechanism, on one history: the stable run's Delta f columns are
+    fed to each variant's QR update, and its least-squares solution is
+    compared with the Householder one at the steps where kappa(F) >= 1e7.
+    CGS-2 keeps ||I - Q^T Q|| at the rounding level and gamma to 1e-8; MGS
+    and ICWY have lost orthogonality (> 1e-6) and err by more than 1e-4."""
+    n = 256
+    G, _ = heat(n, 2)
+    _, _, steps = householder_aa(G, np.zeros(n * n), 10, 34, 0.0)
+    worst = {}
+    for orth in ["mgs", "icwy", "cgs2"]:
+        O = ora.Oracle(n * n, 10, orth)
+        err, loss = 0.0, 0.0
+        for df, f, gamma, dF in steps:
+            assert O.qradd(df) == ora.OK
+            if np.linalg.cond(dF) >= 1e7:
+                go = O.lsq(f)
+                Q, _, _ = O.get_qr()
+                err = max(err, np.linalg.norm(go - gamma) / np.linalg.norm(gamma))
+                loss = max(loss, np.linalg.norm(np.eye(Q.shape[1]) - Q.T @ Q))
+        worst[orth] = (err, loss)
+    assert worst["cgs2"][0] < 1e-8 and worst["cgs2"][1] < 1e-12, worst
+    for orth in ["mgs", "icwy"]:
+        assert worst[orth][0] > 1e-4 and worst[orth][1] > 1e-6, worst
 
 
 # EM for the means of a three-component normal mixture (Sec. 5.3): AA(3),
