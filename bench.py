@@ -14,8 +14,9 @@ Prints one JSON line (rank 0).  With torchrun (N > 1) each rank runs an
 independent replica of the workload (the solve does not shard); value sums
 the iterations of all ranks over the max-over-ranks time.
 
---impl reference times the CPU oracle (oracle/, single thread) on a bounded
-slab of the same workload (406 x 406 x 8), scaled to the full n.
+--impl reference times the CPU oracle (oracle/, its OpenMP build on all the
+host's cores) on the same workload: the full problem when the host has the
+memory for it, else its leading planes, each step timed as it runs.
 """
 from __future__ import annotations
 
@@ -34,7 +35,7 @@ sys.path.insert(0, ROOT)
 
 NX = NY = NZ = 406
 EY, EZ, OMEGA = 0.1, 0.01, 0.8
-SLAB_NZ = 8  # oracle sample: 406 x 406 x 8 rows of the same stencil problem
+SLAB_NZ = 16  # cpu_baseline sample: 406 x 406 x 16 rows of the same stencil problem
 
 
 def size_label(args) -> str:
@@ -521,67 +522,124 @@ def run_wall_to_tol(aa, args, dev):
                         "(the 500-iteration cap of this workload is reached first)", **out}
 
 
-def oracle_sample(args, iters: int, warm: int):
-    """Time the CPU oracle on a 406 x 406 x SLAB_NZ slab of the workload.
-    Returns (seconds per recycle iteration on the slab, slab n)."""
+def host_cores() -> int:
+    """Cores this process may run on (the OpenMP oracle's thread count)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def host_mem_available() -> int:
+    """MemAvailable from /proc/meminfo in bytes (0 when unknown)."""
+    try:
+        with open("/proc/meminfo") as f:
+            for ln in f:
+                if ln.startswith("MemAvailable:"):
+                    return int(ln.split()[1]) * 1024
+    except OSError:
+        pass
+    return 0
+
+
+def oracle_sample(args, nz: int, iters: int, warm: int, threads: int):
+    """Time the CPU oracle on nx x ny x nz rows of the workload (the leading
+    nz planes of the same stencil problem; nz = the full grid's nz runs the
+    whole problem): fill the history (m + 1 steps), `warm` more steps, then
+    `iters` timed recycle iterations (G + step).  threads > 1 uses the
+    OpenMP build; threads == 1 the sequential reference build.
+    Returns (seconds per timed iteration, rows, threads used)."""
     import numpy as np
 
     import aa_synth
     import oracle
-    nx, ny, nz = args.nx, args.ny, SLAB_NZ
+    omp = threads > 1
+    if omp:
+        try:
+            threads = oracle.set_threads(threads)
+        except Exception:  # no OpenMP build on this host: reference build, one thread
+            omp, threads = False, 1
+    nx, ny = args.nx, args.ny
     n = nx * ny * nz
     b = aa_synth.jacobi3d_rhs(0, nx, ny, nz)
-    O = oracle.Oracle(n, args.m, args.orth, store_round={"fp64": 0, "fp32": 1, "bf16": 2}[args.storage])
+    O = oracle.Oracle(n, args.m, args.orth, omp=omp,
+                      store_round={"fp64": 0, "fp32": 1, "bf16": 2}[args.storage])
     x = np.zeros(n)
     for _ in range(args.m + 1 + warm):
-        g = oracle.g_jacobi3d(nx, ny, nz, EY, EZ, OMEGA, b, x)
+        g = oracle.g_jacobi3d(nx, ny, nz, EY, EZ, OMEGA, b, x, omp=omp)
         x, _, _ = O.step(x, g)
     t = []
     for _ in range(iters):
         t0 = time.perf_counter()
-        g = oracle.g_jacobi3d(nx, ny, nz, EY, EZ, OMEGA, b, x)
+        g = oracle.g_jacobi3d(nx, ny, nz, EY, EZ, OMEGA, b, x, omp=omp)
         x, _, _ = O.step(x, g)
         t.append(time.perf_counter() - t0)
     O.close()
-    return t, n
+    return t, n, threads
 
 
 def cpu_baseline(args):
-    t, ns = oracle_sample(args, args.cpu_iters, 0)
+    """The oracle on the host cores, on a bounded slab of the workload
+    (406 x 406 x SLAB_NZ rows): all cores (OpenMP build) and one core
+    (reference build); per-iteration times scaled by rows to the full n."""
     n = args.nx * args.ny * args.nz
-    per_iter_full = statistics.median(t) * n / ns
-    return {"value": round(1.0 / per_iter_full, 5), "unit": "iter/s", "cores": 1,
+    cores = host_cores()
+    t, ns, used = oracle_sample(args, SLAB_NZ, args.cpu_iters, 0, cores)
+    t1, _, _ = oracle_sample(args, SLAB_NZ, 3, 0, 1)
+    full = lambda sec: sec * n / ns
+    return {"value": round(1.0 / full(statistics.median(t)), 5), "unit": "iter/s", "cores": used,
             "kind": "oracle",
             "sample": f"{len(t)} recycle AA({args.m}) {args.orth} iterations (G + step) of the "
-                      f"oracle on a {args.nx}x{args.ny}x{SLAB_NZ} slab of the same stencil problem "
-                      f"(n={ns}), median time scaled by n to the full {n}-row workload",
+                      f"oracle (OpenMP build, {used} threads) on a {args.nx}x{args.ny}x{SLAB_NZ} "
+                      f"slab of the same stencil problem (n={ns}), median time scaled by rows to "
+                      f"the full {n}-row workload",
             "slab_s_per_iter_median": round(statistics.median(t), 4),
-            "slab_s_per_iter_min": round(min(t), 4)}
+            "slab_s_per_iter_min": round(min(t), 4),
+            "one_core": {"value": round(1.0 / full(statistics.median(t1)), 5),
+                         "slab_s_per_iter_median": round(statistics.median(t1), 4),
+                         "slab_s_per_iter_min": round(min(t1), 4), "iters": len(t1),
+                         "build": "sequential reference build"}}
 
 
 def run_reference(args, ws, rank):
+    """--impl reference: the oracle (OpenMP build, all host cores) on the
+    same workload.  It runs the full problem when the host has the memory
+    for it (history and vectors, about (2m + 8) n doubles), else the leading
+    planes of the grid that fit; each step is then timed as it runs and the
+    rate is given per full-size iteration (rows processed / full n)."""
     if rank != 0:
         return None
-    t, ns = oracle_sample(args, args.steps, args.warmup)
     n = args.nx * args.ny * args.nz
-    total_full = sum(t) * n / ns
-    value = args.steps / total_full
+    need_per_plane = (2 * args.m + 8) * args.nx * args.ny * 8
+    avail = host_mem_available()
+    nz = args.nz
+    if avail and need_per_plane * nz > 0.6 * avail:
+        nz = max(1, int(0.6 * avail // need_per_plane))
+    cores = host_cores()
+    t, ns, used = oracle_sample(args, nz, args.steps, args.warmup, cores)
+    frac = ns / n
+    total = sum(t)
+    value = args.steps * frac / total
+    sample = (f"each step: one recycle AA({args.m}) {args.orth} iteration (G + step) of the CPU "
+              f"oracle, OpenMP build on {used} threads, on "
+              + ("the full workload" if nz == args.nz else
+                 f"the leading {nz} of {args.nz} planes (n={ns}; host memory bound), "
+                 f"rate counted per full-size iteration")
+              + f"; min {min(t):.3f} s, median {statistics.median(t):.3f} s per step")
     return {
         "impl": "reference",
         "metric": f"AA iterations/s (3D 7-pt weighted Jacobi, {size_label(args)}, m={args.m}, "
                   f"{args.orth.upper()})",
         "value": round(value, 5), "unit": "iter/s", "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": round(total_full / args.steps * 1e3, 3),
+        "warmup": args.warmup, "ms_per_step": round(total / args.steps * 1e3, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded SplitMix64 b ~ U(-1,1), x0 = 0)",
         "config": {"workload": f"AA({args.m}) {args.orth} on 3D 7-pt weighted Jacobi "
                                f"{args.nx}x{args.ny}x{args.nz}, recycle iterations",
-                   "n": n, "m": args.m, "orth": args.orth, "storage": args.storage},
-        "cpu_baseline": {"value": round(value, 5), "unit": "iter/s", "cores": 1,
-                         "kind": "oracle",
-                         "sample": f"each step: one recycle iteration (G + step) of the CPU "
-                                   f"oracle on a {args.nx}x{args.ny}x{SLAB_NZ} slab (n={ns}), time scaled "
-                                   f"by n to the full workload"},
+                   "n": n, "m": args.m, "orth": args.orth, "storage": args.storage,
+                   "rows_per_step": ns},
+        "cpu_baseline": {"value": round(value, 5), "unit": "iter/s", "cores": used,
+                         "kind": "oracle", "sample": sample},
         "e2e": {"value": round(value, 5), "unit": "iter/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
