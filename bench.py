@@ -72,18 +72,27 @@ def parse():
                    help="jacobi3d: the headline single solve; bratu-batch: 4096 batched Bratu "
                         "solves in one persistent launch; bratu-warmstart: the learned warm "
                         "start on 256^2 Bratu with source (each reported separately)")
-    p.add_argument("--tol-cap", type=int, default=4000)
+    p.add_argument("--tol-cap", type=int, default=10000)
+    p.add_argument("--tol-side", type=int, default=256,
+                   help="jacobi3d-to-tol: grid side of the GPU comparison")
+    p.add_argument("--tol-oracle-side", type=int, default=128,
+                   help="jacobi3d-to-tol: grid side of the comparison with the oracle (0: skip)")
     p.add_argument("--ws-side", type=int, default=128)
     p.add_argument("--ws-train", type=int, default=20000)
     p.add_argument("--ws-test", type=int, default=1000)
     p.add_argument("--ws-epochs", type=int, default=40)
     p.add_argument("--ws-chunk", type=int, default=2432)
     p.add_argument("--ws-max-iters", type=int, default=20000)
+    p.add_argument("--ws-fp64-check", type=int, default=16,
+                   help="bratu-warmstart: held-out instances also solved by sequential FP64 aa_solve "
+                        "from x0 = 0 and from the prediction (0: skip)")
     p.add_argument("--batch-count", type=int, default=4096)
     p.add_argument("--batch-max-iters", type=int, default=100000)
     p.add_argument("--batch-side", type=int, default=0,
                    help="every solve on this grid side (default: log-uniform in [32, 256])")
     p.add_argument("--batch-tol", type=float, default=1e-8)
+    p.add_argument("--batch-vs-seq", type=int, default=32,
+                   help="bratu-batch: sub-batch size solved also by sequential FP64 aa_solve (0: skip)")
     p.add_argument("--batch-shape", default="",
                    help="launch shape BLOCKxCTAS_PER_SM (skips the autotuner)")
     return p.parse_args()
@@ -676,6 +685,7 @@ def run_batch(args, ws, rank, local):
     bulk = t_end <= t99
     bulk_rate = float((it[bulk].astype(np.float64) * n[bulk]).sum()) / (t99 * 1e-3)
     bytes_per_row_iter = 240.0  # FP32 Q/dG, m = 10, recycle: pass A 128 + projection 56 + update 56
+    vs_seq = batch_vs_sequential(aa, args, sides, lams, shape) if args.batch_vs_seq > 0 else None
     if rank != 0:
         return None
     ms_max = max_over_ranks(ms)
@@ -697,26 +707,72 @@ def run_batch(args, ws, rank, local):
                    "autotune_ms": {f"{b}x{c}": round(t, 1) for (b, c), t in tuned.items()}},
         "dtype": "f64 (fp32 history storage)", "data": "synthetic (seeded SplitMix64)",
         "clocks": ck,
+        "vs_sequential_fp64": vs_seq,
     }
 
 
-def run_to_tol(args, ws_, rank, local):
-    """The precision forms against the plain FP64 form at equal final residual:
-    aa_solve on the 406^3 problem from x0 = 0 to ||G(x) - x|| / ||G(0)|| < 1e-8
-    with FP64, FP64 + (hi, lo) arithmetic, FP32 and BF16 history.  Reports
-    iterations, solve time (CUDA events), the final residual, the
-    orthogonality loss ||I - Q^T Q||_F of the final history (host FP64 product)
-    and the distance of the solution from the FP64 form's."""
+def batch_vs_sequential(aa, args, sides, lams, shape):
+    """The batched form against the plain FP64 form on a stated sub-batch:
+    every (count / K)-th solve of the batch (K = --batch-vs-seq, so that the
+    sub-batch spans the side distribution), (a) in one batched launch (FP32
+    history, the batch's launch shape) and (b) one after another with
+    aa_solve (FP64 history, ICWY, m = 10, the built-in Bratu map, the same
+    stop rule ||G(x) - x|| / ||G(0)|| < tol and cap).  Times by CUDA events;
+    both reach the same final residual bound."""
+    import numpy as np
+    import torch
+    K = min(args.batch_vs_seq, len(sides))
+    idx = np.linspace(0, len(sides) - 1, K).round().astype(int)
+    ss, ll = sides[idx], lams[idx]
+    Bs = aa.Batch(ss, ll, m=10, tol=args.batch_tol, max_iters=args.batch_max_iters)
+    ms_b = Bs.solve(*shape)
+    it_b, rs_b, st_b = Bs.results()
+    Bs.close()
+    gfn = aa.builtin_g("aa_g_bratu2d")
+    sp = torch.cuda.current_stream().cuda_stream
+    per, ms_s = [], 0.0
+    for s_, lam in zip(ss, ll):
+        n = int(s_) * int(s_)
+        P = aa.Bratu2D(int(s_), float(lam), None)
+        Pp = aa.C.cast(aa.C.pointer(P), aa.C.c_void_p)
+        z = torch.zeros(n, dtype=torch.float64, device="cuda")
+        g0 = torch.empty_like(z)
+        gfn(z.data_ptr(), g0.data_ptr(), n, sp, Pp)
+        scale = float(torch.linalg.vector_norm(g0))
+        A = aa.Anderson(n, 10, "icwy", "fp64", tol=args.batch_tol, scale=scale,
+                        max_iters=args.batch_max_iters)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        rc, st = A.solve(gfn, P, z)
+        e1.record()
+        torch.cuda.synchronize()
+        ms_s += e0.elapsed_time(e1)
+        per.append((rc == 0, int(st["iters"])))
+        A.close()
+    it_s = np.array([p[1] for p in per])
+    return {"sub_batch": f"{K} solves: every {len(sides) // K}-th of the batch, sides "
+                         f"{int(ss.min())}-{int(ss.max())}",
+            "batched_fp32_ms": round(ms_b, 1), "sequential_fp64_ms": round(ms_s, 1),
+            "speedup": round(ms_s / ms_b, 2),
+            "converged": {"batched": int((st_b == 0).sum()),
+                          "sequential": int(sum(1 for p in per if p[0]))},
+            "iterations": {"batched_sum": int(it_b.sum()), "sequential_sum": int(it_s.sum()),
+                           "max_abs_diff": int(np.abs(it_b - it_s).max())}}
+
+
+def solve_forms(aa, n, nx, ny, nz, m, orth, cap, forms, x_ref=None):
+    """aa_solve from x0 = 0 to ||G(x) - x|| / ||G(0)|| < 1e-8 on the nx x ny x nz
+    3D problem in each (name, storage, flags) form.  Per form: converged,
+    iterations, solve time (CUDA events), final residual, ||I - Q^T Q||_F of
+    the final history and the distance of the solution from x_ref (the first
+    form's solution when None).  Returns (results, x_ref)."""
     import ctypes as C
 
     import numpy as np
     import torch
 
     import aa_synth
-    import paper_2110_09667_gb300 as aa
-    torch.cuda.set_device(local)
-    nx, ny, nz = args.nx, args.ny, args.nz
-    n = nx * ny * nz
     b = torch.from_numpy(aa_synth.jacobi3d_rhs(0, nx, ny, nz)).cuda()
     P = aa.Jacobi3D(nx, ny, nz, EY, EZ, OMEGA, b.data_ptr())
     gfn = aa.builtin_g("aa_g_jacobi3d")
@@ -726,13 +782,10 @@ def run_to_tol(args, ws_, rank, local):
     g0 = torch.empty_like(z)
     gfn(z.data_ptr(), g0.data_ptr(), n, sp, Pp)
     scale = float(torch.linalg.vector_norm(g0))
-    del g0
-    forms = [("fp64", 0), ("fp64", aa.FLAG_DF_ARITH), ("fp32", 0), ("bf16", 0)]
-    out, x_ref = {}, None
-    for storage, flags in forms:
-        name = storage + ("+df" if flags else "")
-        A = aa.Anderson(n, args.m, args.orth, storage, tol=1e-8, scale=scale,
-                        max_iters=args.tol_cap, flags=flags)
+    del g0, z
+    out = {}
+    for name, storage, flags in forms:
+        A = aa.Anderson(n, m, orth, storage, tol=1e-8, scale=scale, max_iters=cap, flags=flags)
         x = torch.zeros(n, dtype=torch.float64, device="cuda")
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
@@ -757,16 +810,72 @@ def run_to_tol(args, ws_, rank, local):
         if x_ref is None:
             x_ref = xh
         out[name] = {"converged": rc == 0, "iterations": st["iters"], "solve_ms": round(ms, 1),
+                     "ms_per_iter": round(ms / max(st["iters"], 1), 4),
                      "final_resid": resid, "orth_loss_final": loss,
-                     "x_rel_diff_vs_fp64": float(np.linalg.norm(xh - x_ref) / np.linalg.norm(x_ref))}
+                     "x_rel_diff": float(np.linalg.norm(xh - x_ref) / np.linalg.norm(x_ref))}
         del A, x
+    return out, x_ref
+
+
+def run_to_tol(args, ws_, rank, local):
+    """The precision forms against the plain FP64 GPU form at equal final
+    residual ||G(x) - x|| / ||G(0)|| < 1e-8 (AA(m), 3D 7-pt weighted Jacobi):
+    (1) on an s^3 grid (--tol-side, default 256: the 406^3 problem needs far
+    more than 10,000 iterations) the FP64, FP32-pipe-dot, FP32-history and
+    BF16-history forms, each with iterations, solve time, final residual,
+    ||I - Q^T Q||_F and the distance of its solution from the FP64 form's;
+    (2) on a grid the oracle solves in minutes (--tol-oracle-side, default
+    128) the same forms against the FP64 oracle's own solution (OpenMP build
+    on the host cores)."""
+    import numpy as np
+    import torch
+
+    import aa_synth
+    import paper_2110_09667_gb300 as aa
+    torch.cuda.set_device(local)
+    forms = [("fp64", "fp64", 0), ("fp64_fp32dots", "fp64", aa.FLAG_FP32_DOTS),
+             ("fp32", "fp32", 0), ("bf16", "bf16", 0)]
+    s = args.tol_side
+    big, _ = solve_forms(aa, s ** 3, s, s, s, args.m, args.orth, args.tol_cap, forms)
+    for name, r in big.items():
+        r["speedup_vs_fp64"] = round(big["fp64"]["solve_ms"] / r["solve_ms"], 3)
+    so = args.tol_oracle_side
+    ora_res = None
+    if so > 0 and rank == 0:
+        import oracle
+        cores = host_cores()
+        try:
+            used = oracle.set_threads(cores)
+            omp = True
+        except Exception:
+            used, omp = 1, False
+        n = so ** 3
+        b = aa_synth.jacobi3d_rhs(0, so, so, so)
+        sc = float(np.linalg.norm(oracle.g_jacobi3d(so, so, so, EY, EZ, OMEGA, b, np.zeros(n))))
+        O = oracle.Oracle(n, args.m, args.orth, omp=omp)
+        t0 = time.perf_counter()
+        r = O.solve({"kind": "jacobi3d", "nx": so, "ny": so, "nz": so, "b": b}, np.zeros(n),
+                    max_iters=args.tol_cap, tol=1e-8, scale=sc)
+        t_ora = time.perf_counter() - t0
+        O.close()
+        small, _ = solve_forms(aa, n, so, so, so, args.m, args.orth, args.tol_cap, forms,
+                               x_ref=r["x"])
+        ora_res = {"grid": f"{so}^3", "oracle": {"iterations": r["iters"],
+                                                 "converged": r["status"] == 0,
+                                                 "seconds": round(t_ora, 1), "threads": used},
+                   "forms_vs_oracle": small}
     if rank != 0:
         return None
     return {"metric": f"time to ||f||/||G(0)|| < 1e-8, AA({args.m}) {args.orth}, 3D 7-pt weighted "
-                      f"Jacobi {nx}x{ny}x{nz}, by history precision",
-            "value": out["fp64"]["solve_ms"], "unit": "ms", "n_gpus": ws_,
-            "higher_is_better": False, "forms": out, "cap": args.tol_cap,
-            "data": "synthetic (seeded SplitMix64 b ~ U(-1,1), x0 = 0)"}
+                      f"Jacobi {s}^3, by history precision",
+            "value": big["fp64"]["solve_ms"], "unit": "ms", "n_gpus": ws_,
+            "higher_is_better": False, "cap": args.tol_cap,
+            "forms": big, "oracle_check": ora_res,
+            "data": "synthetic (seeded SplitMix64 b ~ U(-1,1), x0 = 0)",
+            "notes": "x_rel_diff: distance from the FP64 GPU solution (forms) or from the FP64 "
+                     "oracle's solution (forms_vs_oracle); the FP32-history form stores Q and dG in "
+                     "FP32 and runs its n-space updates in FP32, dot products accumulate to about "
+                     "2^-44 and are summed in FP64, R, T and gamma are FP64"}
 
 
 def run_warmstart(args, ws_, rank, local):
@@ -829,6 +938,8 @@ def run_warmstart(args, ws_, rank, local):
     inf_ms = (time.perf_counter() - t0) * 1e3
     _, it_w, st_w, ms_w, fb = solve_chunks(te, x0=x0.astype(np.float64))
     good = st_c == 0
+    fp64 = warm_vs_plain_fp64(aa, args, te[:args.ws_fp64_check], x0[:args.ws_fp64_check], s) \
+        if args.ws_fp64_check > 0 else None
     if rank != 0:
         return None
 
@@ -856,8 +967,62 @@ def run_warmstart(args, ws_, rank, local):
         "train": {"loss_first": hist[0], "loss_last": hist[-1], "ms": round(train_ms, 1),
                   "steps": steps, "gemm_tflops": round(gemm_flop * steps / (train_ms * 1e-3) / 1e12, 2),
                   "data_solve_ms": round(ms_tr, 1)},
+        "plain_fp64_aa_solve": fp64,
         "total_s": round(time.perf_counter() - t_all, 1),
     }
+
+
+def warm_vs_plain_fp64(aa, args, seeds, x0s, s):
+    """The warm start against the plain FP64 GPU form: the first K held-out
+    instances (K = --ws-fp64-check) solved one after another with aa_solve
+    (FP64 history, ICWY, m = 10, the built-in Bratu-with-source map, stop at
+    ||G(x) - x|| / ||G(0)|| < 1e-8, the workload's cap), from x0 = 0 and from
+    the MLP prediction (gated: used only if ||G(x0) - x0|| < ||G(0)||).
+    Iterations and CUDA-event wall per form, prediction time excluded (it is
+    reported for the batched run)."""
+    import numpy as np
+    import torch
+
+    from paper_2110_09667_gb300 import warmstart as W
+    n = s * s
+    lam, _, src = W.instances(seeds, s)
+    gfn = aa.builtin_g("aa_g_bratu2d")
+    sp = torch.cuda.current_stream().cuda_stream
+    rec = {"cold": [], "warm": []}
+    ms = {"cold": 0.0, "warm": 0.0}
+    fallbacks = 0
+    for i in range(len(seeds)):
+        srcd = torch.from_numpy(np.ascontiguousarray(src[i], dtype=np.float64)).cuda()
+        P = aa.Bratu2D(s, float(lam[i]), srcd.data_ptr())
+        Pp = aa.C.cast(aa.C.pointer(P), aa.C.c_void_p)
+        z = torch.zeros(n, dtype=torch.float64, device="cuda")
+        g = torch.empty_like(z)
+        gfn(z.data_ptr(), g.data_ptr(), n, sp, Pp)
+        scale = float(torch.linalg.vector_norm(g))
+        xw = torch.from_numpy(np.ascontiguousarray(x0s[i], dtype=np.float64)).cuda()
+        gfn(xw.data_ptr(), g.data_ptr(), n, sp, Pp)
+        if not float(torch.linalg.vector_norm(g - xw)) < scale:
+            xw.zero_()
+            fallbacks += 1
+        for kind, x in (("cold", z), ("warm", xw)):
+            A = aa.Anderson(n, 10, "icwy", "fp64", tol=1e-8, scale=scale,
+                            max_iters=args.ws_max_iters)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            rc, st = A.solve(gfn, P, x)
+            e1.record()
+            torch.cuda.synchronize()
+            ms[kind] += e0.elapsed_time(e1)
+            rec[kind].append((rc == 0, int(st["iters"])))
+            A.close()
+    out = {"instances": len(seeds), "gate_fallbacks": fallbacks}
+    for kind in ("cold", "warm"):
+        its = np.array([r[1] for r in rec[kind]])
+        out[kind] = {"wall_ms": round(ms[kind], 1), "iters_mean": round(float(its.mean()), 1),
+                     "converged": int(sum(1 for r in rec[kind] if r[0]))}
+    out["speedup"] = round(ms["cold"] / ms["warm"], 3)
+    return out
 
 
 def main():

@@ -14,9 +14,12 @@
 // applies the QRDelete rotation and accumulates the first block of dot
 // products; warp 0 updates R and T; the projection pass forms the new
 // column; warp 0 solves for gamma; the update pass writes x_{i+1}.
-// Q and dG are stored in FP32 (the precision form) and every operation on
-// them runs on the FP32/INT pipes (aa_df.cuh); x, G(x), f, Delta f stay FP64,
-// and R, T, gamma are FP64.
+// Q and dG are stored in FP32 (the precision form) and the n-space arithmetic
+// on them runs in FP32 (the rotation with float multipliers; projection and
+// update sums with (hi, lo) float coefficients, each part in its own chain);
+// dot products are exact float products summed in compensated float pairs
+// and folded into FP64 (aa_df.cuh); x, G(x), f, Delta f stay FP64, and R, T,
+// gamma are FP64.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -444,21 +447,21 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : (NT <= 256 ? 2 : 1)) batch
         for (int jj = 0; jj < MB; ++jj)
           if (jj < c) qv[jj] = SQ(sgA, jj);
         if (del) {
-          F2 wv{qv[0], 0.f};
+          // the scaled rotations in FP32, two multiply-adds each: the two
+          // forms differ in which of (carry w, stored column u) meets which
+          // multiplier, out = b + k1 a, carry = a + k2 b with (a, b) = (u, w)
+          // when |c| >= |s| and (w, u) otherwise
+          float wv = qv[0];
 #pragma unroll
           for (int jj = 0; jj < MB - 1; ++jj) {
             if (jj < m - 1) {
               const float u = qv[jj + 1];
-              const F2 k1{cfr[4 * jj], cfr[4 * jj + 1]}, k2{cfr[4 * jj + 2], cfr[4 * jj + 3]};
-              // the two scaled-rotation forms as one: operands selected, so
-              // that exactly two (hi, lo) multiply-adds are issued
               const bool ty = __double_as_longlong(st.rot[4 * jj + 2]) != 0;
-              const F2 P = aa::df_axpy_f(wv, ty ? k1 : k2, u);   // w + kp u
-              const F2 Qv = aa::df_axpy_ff(u, ty ? k2 : k1, wv);  // u + kq w
-              const F2 out = ty ? P : Qv;
-              wv = ty ? Qv : P;
-              qv[jj] = out.h;
-              a.Q[(int64_t)jj * a.N + off + r] = out.h;
+              const float pa = ty ? u : wv, pb = ty ? wv : u;
+              const float o = __fmaf_rn(cfr[4 * jj], pa, pb);
+              wv = __fmaf_rn(cfr[4 * jj + 2], pb, pa);
+              qv[jj] = o;
+              a.Q[(int64_t)jj * a.N + off + r] = o;
             }
           }
         }
@@ -582,10 +585,18 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : (NT <= 256 ? 2 : 1)) batch
           stageP(r + NT, sgP ^ 1);
           prefetch_rows(lane, r - lane + PF * NT, n, a.Q + off, a.N, k, DF, FP, nullptr, nullptr);
           cp_async_wait<1>();
-          F2 acc = aa::d2f2(SD(sgP, 0));
+          // v = Delta f - Q r: FP32 chains of the coefficients' heads and
+          // tails over the stored columns, added to Delta f in FP64
+          float s0 = 0.f, s1 = 0.f, sl = 0.f;
 #pragma unroll
           for (int jj = 0; jj < MB; ++jj)
-            if (jj < k) acc = aa::df_axpy_f(acc, F2{cfc[2 * jj], cfc[2 * jj + 1]}, SQ(sgP, jj));
+            if (jj < k) {
+              const float qj = SQ(sgP, jj);
+              if (jj & 1) s1 = __fmaf_rn(cfc[2 * jj], qj, s1);
+              else s0 = __fmaf_rn(cfc[2 * jj], qj, s0);
+              sl = __fmaf_rn(cfc[2 * jj + 1], qj, sl);
+            }
+          const F2 acc = aa::d2f2(SD(sgP, 0) + (aa::f2d(__fadd_rn(s0, s1)) + aa::f2d(sl)));
           float p, q;
           aa::prod_ff(acc, F2{cfv[0], cfv[1]}, p, q);
           a.Q[(int64_t)k * a.N + off + r] = __fadd_rn(p, q);
@@ -635,12 +646,17 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : (NT <= 256 ? 2 : 1)) batch
           Xn[r] = SD(sgU, 0);
           continue;
         }
-        F2 acc = aa::d2f2(SD(sgU, 0));
+        // x_{i+1} = G(x_i) - dG gamma: FP32 chains (heads, tails), added in FP64
+        float s0 = 0.f, s1 = 0.f, sl = 0.f;
 #pragma unroll
         for (int jj = 0; jj < MB; ++jj)
-          if ((gmask >> jj) & 1u)
-            acc = aa::df_axpy_f(acc, F2{cfg[2 * jj], cfg[2 * jj + 1]}, SQ(sgU, jj));
-        Xn[r] = aa::f22d(acc);
+          if ((gmask >> jj) & 1u) {
+            const float dj = SQ(sgU, jj);
+            if (jj & 1) s1 = __fmaf_rn(cfg[2 * jj], dj, s1);
+            else s0 = __fmaf_rn(cfg[2 * jj], dj, s0);
+            sl = __fmaf_rn(cfg[2 * jj + 1], dj, sl);
+          }
+        Xn[r] = SD(sgU, 0) + (aa::f2d(__fadd_rn(s0, s1)) + aa::f2d(sl));
       }
       cp_async_wait<0>();
       __syncthreads();

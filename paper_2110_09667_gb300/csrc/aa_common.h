@@ -20,7 +20,7 @@ constexpr int NWARP = NT / 32;
 constexpr int MMAX = 64;                // largest history depth
 constexpr int MAXCOL = MMAX + 6;        // most columns one pass stages
 constexpr int NDOT_MAX = 256;           // most dot products one pass reduces
-constexpr int STAGES = 2;               // tile pipeline depth
+constexpr int STAGES = 3;               // deepest tile pipeline (tiles in flight per CTA)
 
 // Pass kinds.
 enum PassKind : int {

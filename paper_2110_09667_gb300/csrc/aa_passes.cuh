@@ -118,15 +118,21 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 
 // ------------------------------------------------------------- tile access
 
+// Stage layout: the FP64 columns 0..qbase-1 first (TR doubles each; the
+// FP32-pipe forms overwrite them in place with (hi, lo) float pairs), then
+// the history columns at their storage width (TR elements each), so that an
+// FP32 or BF16 history stage takes a half or a quarter of the FP64 space.
 struct Stage {
   unsigned char *base;
-  __device__ __forceinline__ double *d(int c) const { return (double *)(base + (size_t)c * TR * 8); }
+  int qbase;
+  __device__ __forceinline__ double *d(int c) const { return (double *)(base + c * (TR * 8)); }
   template <class QT>
   __device__ __forceinline__ QT *q(int c) const {
-    return (QT *)(base + (size_t)c * TR * 8);
+    if constexpr (sizeof(QT) == 8) return (QT *)(base + c * (TR * 8));
+    else return (QT *)(base + qbase * (TR * 8) + (c - qbase) * (int)(TR * sizeof(QT)));
   }
   // an FP64 column after it was split in place into (hi, lo) floats
-  __device__ __forceinline__ float2 *p(int c) const { return (float2 *)(base + (size_t)c * TR * 8); }
+  __device__ __forceinline__ float2 *p(int c) const { return (float2 *)(base + c * (TR * 8)); }
   __device__ __forceinline__ F2 f2(int c, int r) const {
     const float2 v = p(c)[r];
     return F2{v.x, v.y};
@@ -137,6 +143,13 @@ struct Stage {
 template <class QT>
 __device__ __forceinline__ int col_esz(const PassArgs &a, int c) {
   return c >= a.qbase ? (int)sizeof(QT) : 8;
+}
+
+// Bytes of one stage (see Stage), a multiple of 128.
+template <class QT>
+__host__ __device__ __forceinline__ size_t stage_size(const PassArgs &a) {
+  const size_t b = (size_t)a.qbase * TR * 8 + (size_t)(a.ncol - a.qbase) * TR * sizeof(QT);
+  return (b + 127) / 128 * 128;
 }
 
 // Issue the bulk copies of tile t into stage st (one thread).  Rows are
@@ -151,10 +164,12 @@ static __device__ void issue_tile(const PassArgs &a, Stage st, int t, uint64_t *
   for (int c = 0; c < a.ncol; ++c) bytes += (uint32_t)(rt * col_esz<QT>(a, c));
   mbar_arrive_expect_tx(bar, bytes);
   if (rt > 0) {
+    size_t off = 0;
     for (int c = 0; c < a.ncol; ++c) {
       const int es = col_esz<QT>(a, c);
       const char *src = (const char *)a.col[c] + r0 * es;
-      bulk_g2s(st.base + (size_t)c * TR * 8, src, (uint32_t)(rt * es), bar);
+      bulk_g2s(st.base + off, src, (uint32_t)(rt * es), bar);
+      off += (size_t)TR * es;
     }
   }
 }
@@ -168,6 +183,23 @@ __device__ __forceinline__ void load_tail_row(const PassArgs &a, Stage st, int t
     else
       st.d(c)[r] = ((const double *)a.col[c])[row];
   }
+}
+
+// Rows r and r + 1 (r even) of a stored history column as floats.
+template <class QT>
+__device__ __forceinline__ float2 q2rows(Stage st, int c, int r);
+template <>
+__device__ __forceinline__ float2 q2rows<float>(Stage st, int c, int r) {
+  return *(const float2 *)(st.q<float>(c) + r);
+}
+template <>
+__device__ __forceinline__ float2 q2rows<__nv_bfloat16>(Stage st, int c, int r) {
+  return __bfloat1622float2(*(const __nv_bfloat162 *)(st.q<__nv_bfloat16>(c) + r));
+}
+template <>
+__device__ __forceinline__ float2 q2rows<double>(Stage st, int c, int r) {  // not called
+  const double *q = st.q<double>(c) + r;
+  return make_float2((float)q[0], (float)q[1]);
 }
 
 template <class QT>
@@ -296,14 +328,58 @@ __device__ __forceinline__ void row_program(const PassArgs &a, Stage st, int t, 
   }
 }
 
-// Row programs with every n-space operation on the FP32/INT pipes, for
-// FP32/BF16 history storage.  FP64 inputs are split into (hi, lo) floats,
-// stored history entries are floats (exact), the residual differences stay
-// FP64 (3 adds per row).  Columns that feed the dot phase are left in shared
-// memory as (hi, lo) pairs.
+// Row programs of the FP32/BF16-history form (MODE 2).  The history columns
+// are stored in FP32 or BF16, and the n-space arithmetic on them runs in FP32
+// on the FP32 pipe: the QRDelete rotation (two multiply-adds per rotation,
+// multipliers rounded to float), the Gram-Schmidt projections v = w - Q c
+// (the CGS-2 middle pass and an MGS link alike) and the update
+// x = g - dG gamma.  The projection and update coefficients are FP64 and
+// enter as (hi, lo) float pairs, each part in its own multiply-add chain
+// (lp_chain): a coefficient rounded to float would leave an error along the
+// history columns themselves, inside span(Q).  The float multipliers of the
+// rotation make each rotated pair orthogonal only to about the float unit
+// roundoff u = 2^-24 (adding their tails after a rounded multiply-add would
+// round away), and that sets this form's orthogonality loss, about
+// u sqrt(m); the storage rounding alone gives random errors, about u / sqrt(n)
+// per inner product.  The vectors x, G(x), f, Delta f, v and y stay FP64:
+// the residual differences are FP64 adds, and a projection or update sum is
+// added to its FP64 vector in FP64.  Dot products stay exact to about 2^-44:
+// those whose two operands are FP64 vectors (squared norms, v.f, Delta f.f)
+// accumulate row by row in FP64 registers (dv0, dv1 return the row's values
+// of FP64 columns 0 and 1 for that); those with a history column run in the
+// dot phase on (hi, lo) splits of the FP64 operands, which the row program
+// leaves in shared memory for the columns set in `split`.
+
+// sum_j c_j q_j over cnt stored columns q_j = stage column qb + j (row r),
+// c_j given as (hi, lo) float pairs at c[2j], c[2j+1]: two FP32 chains of
+// the heads (independent, for latency) and one of the tails, returned as an
+// FP64 value (converted by integer operations: the hardware float <-> double
+// conversions occupy the FP64 pipe, which is the scarce unit on this part).
 template <class QT>
-__device__ __forceinline__ void row_program_df(const PassArgs &a, Stage st, int t, int r,
-                                               const double *co, const float *cf) {
+__device__ __forceinline__ double lp_chain(Stage st, const float *c, int qb, int cnt, int r) {
+  float s0 = 0.f, s1 = 0.f, sl = 0.f;
+  int j = 0;
+  for (; j + 1 < cnt; j += 2) {
+    const float2 c0 = *(const float2 *)(c + 2 * j), c1 = *(const float2 *)(c + 2 * j + 2);
+    const float q0 = q2f<QT>(st.q<QT>(qb + j)[r]), q1 = q2f<QT>(st.q<QT>(qb + j + 1)[r]);
+    s0 = __fmaf_rn(c0.x, q0, s0);
+    s1 = __fmaf_rn(c1.x, q1, s1);
+    sl = __fmaf_rn(c0.y, q0, sl);
+    sl = __fmaf_rn(c1.y, q1, sl);
+  }
+  if (j < cnt) {
+    const float2 cc = *(const float2 *)(c + 2 * j);
+    const float q0 = q2f<QT>(st.q<QT>(qb + j)[r]);
+    s0 = __fmaf_rn(cc.x, q0, s0);
+    sl = __fmaf_rn(cc.y, q0, sl);
+  }
+  return f2d(__fadd_rn(s0, s1)) + f2d(sl);
+}
+
+template <class QT>
+__device__ __forceinline__ void row_program_lp(const PassArgs &a, Stage st, int t, int r,
+                                               const double *co, const float *cf, uint32_t split,
+                                               double &dv0, double &dv1) {
   const int64_t row = (int64_t)t * TR + r;
   switch (a.kind) {
     case K_INIT: {
@@ -312,42 +388,44 @@ __device__ __forceinline__ void row_program_df(const PassArgs &a, Stage st, int 
       a.out_f[row] = f;
       a.out_g[row] = g;
       a.out_x[row] = g;
-      st.put(0, r, d2f2(f));
+      dv0 = f;
       break;
     }
     case K_A: {
-      double df;
+      double df, f = 0.0;
       if (a.step_mode) {
         const double x = st.d(0)[r], g = st.d(1)[r], gp = st.d(2)[r], fp = st.d(3)[r];
-        const double f = g - x;
+        f = g - x;
         df = f - fp;
         const double dg = g - gp;
-        ((QT *)a.out_dg)[row] = from_d<QT>(dg);
+        ((QT *)a.out_dg)[row] = f2q<QT>(d2f_rn(dg));
         a.out_f[row] = f;
         a.out_g[row] = g;
-        st.put(0, r, d2f2(f));
-        st.put(1, r, d2f2(df));
+        dv0 = f;
+        dv1 = df;
+        if (split & 1u) st.put(0, r, d2f2(f));
+        if (split & 2u) st.put(1, r, d2f2(df));
       } else {
         df = st.d(0)[r];
-        st.put(0, r, d2f2(df));
+        dv0 = df;
+        if (split & 1u) st.put(0, r, d2f2(df));
       }
       a.out_df[row] = df;
-      if (a.k == 0) ((QT *)a.out_q[0])[row] = from_d<QT>(df);
+      if (a.k == 0) ((QT *)a.out_q[0])[row] = f2q<QT>(d2f_rn(df));
       if (a.del) {
-        // QRDelete rotation (scaled form, see row_program) in (hi, lo) floats.
+        // QRDelete: the scaled Givens rotations of row_program in FP32.  The
+        // two forms differ in which of (carry w, stored column u) meets
+        // which multiplier: out = b + k1 a, carry = a + k2 b with
+        // (a, b) = (u, w) when |c| >= |s| and (w, u) otherwise.
         const int qb = a.qbase;
-        F2 w{q2f<QT>(st.q<QT>(qb)[r]), 0.f};
+        float w = q2f<QT>(st.q<QT>(qb)[r]);
         for (int j = 0; j < a.m - 1; ++j) {
           const float u = q2f<QT>(st.q<QT>(qb + j + 1)[r]);
-          const float *R = cf + CF_ROT + 4 * j;
-          const F2 k1{R[0], R[1]}, k2{R[2], R[3]};
-          // both forms as one (operands selected, see row_program)
+          const float4 k = *(const float4 *)(cf + CF_ROT + 4 * j);  // k1 (hi, lo), k2 (hi, lo)
           const bool ty = __double_as_longlong(co[CO_ROT + 4 * j + 2]) != 0;
-          const F2 P = df_axpy_f(w, ty ? k1 : k2, u);   // w + kp u
-          const F2 Qv = df_axpy_ff(u, ty ? k2 : k1, w);  // u + kq w
-          const F2 out = ty ? P : Qv;
-          w = ty ? Qv : P;
-          const QT qs = f2q<QT>(out.h);
+          const float pa = ty ? u : w, pb = ty ? w : u;
+          const QT qs = f2q<QT>(__fmaf_rn(k.x, pa, pb));
+          w = __fmaf_rn(k.z, pb, pa);
           ((QT *)a.out_q[j])[row] = qs;
           st.q<QT>(qb + j)[r] = qs;
         }
@@ -356,54 +434,58 @@ __device__ __forceinline__ void row_program_df(const PassArgs &a, Stage st, int 
     }
     case K_PROJ: {
       const int qb = a.qbase;
-      F2 acc = d2f2(st.d(0)[r]);
       if (a.orth == O_DCGS2 && (a.flags & 0x100u)) {
+        // DCGS-2: correct q_{k-1} against q_0..q_{k-2}, store it, then
+        // project against the corrected factor
         const int kk = a.k - 1;
-        float p, e;
-        prod_f(F2{cf[CF_MISC], cf[CF_MISC + 1]}, q2f<QT>(st.q<QT>(qb + kk)[r]), p, e);
-        F2 qn = fast_two_sum(p, e);
-        for (int j = 0; j < kk; ++j)
-          qn = df_axpy_f(qn, F2{cf[CF_COEF2 + 2 * j], cf[CF_COEF2 + 2 * j + 1]},
-                         q2f<QT>(st.q<QT>(qb + j)[r]));
-        const QT qs = f2q<QT>(qn.h);
+        const float qk = q2f<QT>(st.q<QT>(qb + kk)[r]);
+        float qn = cf[CF_MISC] * qk, ql = cf[CF_MISC + 1] * qk;
+        for (int j = 0; j < kk; ++j) {
+          const float2 c = *(const float2 *)(cf + CF_COEF2 + 2 * j);
+          const float q = q2f<QT>(st.q<QT>(qb + j)[r]);
+          qn = __fmaf_rn(c.x, q, qn);
+          ql = __fmaf_rn(c.y, q, ql);
+        }
+        qn += ql;
+        const QT qs = f2q<QT>(qn);
         ((QT *)a.out_q[kk])[row] = qs;
         st.q<QT>(qb + kk)[r] = qs;
       }
-      for (int j = a.j0; j < a.k; ++j)
-        acc = df_axpy_f(acc, F2{cf[CF_COEF + 2 * j], cf[CF_COEF + 2 * j + 1]},
-                        q2f<QT>(st.q<QT>(qb + j - a.j0)[r]));
-      float p, e;
-      prod_ff(acc, F2{cf[CF_MISC + 2], cf[CF_MISC + 3]}, p, e);
-      ((QT *)a.out_q[a.k])[row] = f2q<QT>(__fadd_rn(p, e));
-      st.put(0, r, acc);
-      if (a.step_mode) st.put(1, r, d2f2(st.d(1)[r]));  // f feeds v.f (and q_{k-1}.f)
+      // v = w - Q coef (the coefficients are stored negated), added to w in FP64
+      const double v = st.d(0)[r] + lp_chain<QT>(st, cf + CF_COEF + 2 * a.j0, qb, a.k - a.j0, r);
+      {
+        // the stored column v / ||Delta f||: (hi, lo) split of v times the
+        // (hi, lo) scale on the FP32 pipe
+        float p, e;
+        prod_ff(d2f2(v), F2{cf[CF_MISC + 2], cf[CF_MISC + 3]}, p, e);
+        ((QT *)a.out_q[a.k])[row] = f2q<QT>(__fadd_rn(p, e));
+      }
+      dv0 = v;
+      if (a.step_mode) {
+        const double f = st.d(1)[r];
+        dv1 = f;
+        if (split & 2u) st.put(1, r, d2f2(f));  // f meets q_{k-1} (DCGS-2)
+      }
       break;
     }
     case K_CGS2B: {
-      F2 acc = d2f2(st.d(0)[r]);
-      for (int j = 0; j < a.k; ++j)
-        acc = df_axpy_f(acc, F2{cf[CF_COEF + 2 * j], cf[CF_COEF + 2 * j + 1]},
-                        q2f<QT>(st.q<QT>(a.qbase + j)[r]));
-      a.out_df[row] = f22d(acc);
-      st.put(0, r, acc);
+      const double y = st.d(0)[r] + lp_chain<QT>(st, cf + CF_COEF, a.qbase, a.k, r);
+      a.out_df[row] = y;
+      dv0 = y;
+      st.put(0, r, d2f2(y));
       break;
     }
     case K_MGS: {
-      F2 acc = d2f2(st.d(0)[r]);
-      acc = df_axpy_f(acc, F2{cf[CF_COEF + 2 * (a.jm - 1)], cf[CF_COEF + 2 * (a.jm - 1) + 1]},
-                      q2f<QT>(st.q<QT>(a.qbase)[r]));
-      a.out_df[row] = f22d(acc);
-      st.put(0, r, acc);
+      const double v = st.d(0)[r] + lp_chain<QT>(st, cf + CF_COEF + 2 * (a.jm - 1), a.qbase, 1, r);
+      a.out_df[row] = v;
+      dv0 = v;
+      st.put(0, r, d2f2(v));
       break;
     }
     case K_UPDATE: {
-      F2 acc = d2f2(st.d(0)[r]);
-      for (int i = 0; i < a.ng; ++i)
-        acc = df_axpy_f(acc, F2{cf[CF_COEF + 2 * i], cf[CF_COEF + 2 * i + 1]},
-                        q2f<QT>(st.q<QT>(a.qbase + i)[r]));
-      const double xn = f22d(acc);
+      const double xn = st.d(0)[r] + lp_chain<QT>(st, cf + CF_COEF, a.qbase, a.ng, r);
       a.out_x[row] = xn;
-      if (a.stop_kind == 1) st.put(1, r, d2f2(xn - st.d(1)[r]));
+      if (a.stop_kind == 1) dv1 = xn - st.d(1)[r];
       break;
     }
     case K_LSQ: {
@@ -957,6 +1039,13 @@ static __device__ int dot_col_exp(const PassArgs &a, const DevState *S, int c) {
   return pow2_of_rms(sg * sg * n, true, 0);
 }
 
+// A float partial sum into FP64 (exact), by integer operations: the
+// hardware conversion runs on the FP64 pipe, which is the scarce unit here.
+template <int MODE>
+__device__ __forceinline__ double fold_f(float x) {
+  return f2d(x);
+}
+
 // 2^e as a double, e in [-1022, 1023] (exact).
 __device__ __forceinline__ double pow2d(int e) {
   return __hiloint2double((1023 + e) << 20, 0);
@@ -984,7 +1073,7 @@ __global__ void __launch_bounds__(NT) pass_kernel(const __grid_constant__ PassAr
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t bars[STAGES];
   __shared__ double co[CO_SIZE];
-  __shared__ float cf[MODE >= 2 ? CF_SIZE : 1];
+  __shared__ __align__(16) float cf[MODE >= 2 ? CF_SIZE : 4];
   __shared__ uint8_t sda[NDOT_MAX], sdb[NDOT_MAX];
   __shared__ int s_last;
   __shared__ int s_err;
@@ -997,7 +1086,7 @@ __global__ void __launch_bounds__(NT) pass_kernel(const __grid_constant__ PassAr
 
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
-  const size_t stage_bytes = (size_t)a.ncol * TR * 8;
+  const size_t stage_bytes = stage_size<QT>(a);
   DevState *S = a.st;
 
   // Per-pass coefficients from the device state (written by earlier passes).
@@ -1025,6 +1114,24 @@ __global__ void __launch_bounds__(NT) pass_kernel(const __grid_constant__ PassAr
       }
       s_split[0] = sm[0];
       s_split[1] = sm[1];
+      s_n64 = n64;
+    }
+  }
+  if constexpr (MODE == 2) {
+    // leading dots of two FP64 vectors: FP64 row-local sums; FP64 columns
+    // that meet a history column in a later dot are split for the dot phase
+    if (tid == 0) {
+      int n64 = 0;
+      while (n64 < a.ndots && n64 < RD && a.dot_a[n64] < a.qbase && a.dot_b[n64] < a.qbase &&
+             a.dot_a[n64] < 2 && a.dot_b[n64] < 2)
+        ++n64;
+      uint64_t sm = 0ull;
+      for (int d = n64; d < a.ndots; ++d) {
+        if (a.dot_a[d] < a.qbase) sm |= 1ull << a.dot_a[d];
+        if (a.dot_b[d] < a.qbase) sm |= 1ull << a.dot_b[d];
+      }
+      s_split[0] = sm;
+      s_split[1] = 0ull;
       s_n64 = n64;
     }
   }
@@ -1079,16 +1186,18 @@ __global__ void __launch_bounds__(NT) pass_kernel(const __grid_constant__ PassAr
   if (tid == 0) {
     for (int s = 0; s < nstages; ++s) {
       const int t = blockIdx.x + s * gridDim.x;
-      if (t < a.ntiles) issue_tile<QT>(a, Stage{smem + s * stage_bytes}, t, &bars[s]);
+      if (t < a.ntiles) issue_tile<QT>(a, Stage{smem + s * stage_bytes, a.qbase}, t, &bars[s]);
     }
   }
 
   double acc[DPW];
   float accS[MODE ? DPW : 1], accC[MODE ? DPW : 1];
-  constexpr int NRD = ((DPW == 1 && MODE == 0) || MODE == 1) ? RD : 1;
-  const bool rowdots = (DPW == 1) && (MODE == 0) && a.ndots <= RD;
-  // first dot of the warp-per-dot phase (MODE 1: after the FP64 norms)
-  const int dbase = (MODE == 1) ? s_n64 : 0;
+  constexpr int NRD = ((DPW == 1 && MODE == 0) || MODE == 1 || MODE == 2) ? RD : 1;
+  // every dot product accumulated row by row in FP64 (no dot phase)
+  const bool rowdots = ((DPW == 1) && (MODE == 0) && a.ndots <= RD) ||
+                       (MODE == 2 && s_n64 == a.ndots);
+  // first dot of the warp-per-dot phase (MODE 1, 2: after the FP64 row dots)
+  const int dbase = (MODE == 1 || MODE == 2) ? s_n64 : 0;
   double racc[NRD];
 #pragma unroll
   for (int d = 0; d < NRD; ++d) racc[d] = 0.0;
@@ -1098,18 +1207,32 @@ __global__ void __launch_bounds__(NT) pass_kernel(const __grid_constant__ PassAr
 #pragma unroll
     for (int i = 0; i < DPW; ++i) accS[i] = accC[i] = 0.f;
   }
-  constexpr int FLUSH = (MODE == 2) ? 2 : (MODE == 3 ? 4 : 8);  // tiles per fold into FP64
+  constexpr int FLUSH = (MODE == 3) ? 4 : 8;  // tiles per fold into FP64
 
+  constexpr bool EARLY_REFILL = (MODE == 1 || MODE == 2);
   int it = 0;
   for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++it) {
     const int s = it % nstages;
     const uint32_t parity = (uint32_t)((it / nstages) & 1);
-    Stage st{smem + s * stage_bytes};
+    Stage st{smem + s * stage_bytes, a.qbase};
     const int rows = (int)min((int64_t)TR, a.n - (int64_t)t * TR);
     const int rt = rows & ~7;
     if (!mbar_wait_bounded(&bars[s], parity)) s_err = 1;
     __syncthreads();
     if (s_err) break;
+    // FP32-pipe dot forms with two or more stages: the stage consumed in the
+    // previous iteration is refilled here, since the barrier above already
+    // ordered every thread's last use of it, so the tile loop needs no
+    // barrier at its end.  (The exact FP64 form keeps the refill at the end:
+    // there the early one costs registers and occupancy.)
+    if (EARLY_REFILL && nstages > 1 && tid == 0 && it > 0) {
+      const int tn = t + (nstages - 1) * (int)gridDim.x;
+      if (tn < a.ntiles) {
+        const int sp = (it - 1) % nstages;
+        fence_proxy_async();
+        issue_tile<QT>(a, Stage{smem + sp * stage_bytes, a.qbase}, tn, &bars[sp]);
+      }
+    }
     if (tid >= rt && tid < rows) load_tail_row<QT>(a, st, t, tid);
     if (tid < rows) {
       if constexpr (MODE == 3) {
@@ -1120,7 +1243,15 @@ __global__ void __launch_bounds__(NT) pass_kernel(const __grid_constant__ PassAr
           if ((a.dotcols[c >> 6] & bit) && !(cv[c >> 6] & bit)) st.put(c, tid, d2f2(st.d(c)[tid]));
         }
       } else if constexpr (MODE == 2) {
-        row_program_df<QT>(a, st, t, tid, co, cf);
+        double dv0 = 0.0, dv1 = 0.0;
+        row_program_lp<QT>(a, st, t, tid, co, cf, (uint32_t)s_split[0], dv0, dv1);
+#pragma unroll
+        for (int d = 0; d < NRD; ++d) {
+          if (d < dbase) {
+            const double va = sda[d] ? dv1 : dv0, vb = sdb[d] ? dv1 : dv0;
+            racc[d] = fma(va, vb, racc[d]);
+          }
+        }
       } else {
         row_program<QT>(a, st, t, tid, co);
         if constexpr (MODE == 1) {
@@ -1168,7 +1299,35 @@ __global__ void __launch_bounds__(NT) pass_kernel(const __grid_constant__ PassAr
         } else {
           const bool qa = (MODE == 2) && ca >= a.qbase, qb = (MODE == 2) && cb >= a.qbase;
           float S = accS[i], C = accC[i], p, e;
-          if (qa && qb) {
+          if (MODE == 2 && rows == TR && (qa || qb)) {
+            // full tile: lane l takes row pairs 2l + 64h (8-byte history
+            // loads, 16-byte pair loads: contiguous across the warp)
+            if (qa && qb) {
+#pragma unroll
+              for (int h = 0; h < TR / 64; ++h) {
+                const int r = 2 * lane + 64 * h;
+                const float2 x = q2rows<QT>(st, ca, r), y = q2rows<QT>(st, cb, r);
+                p = __fmul_rn(x.x, y.x);
+                e = __fmaf_rn(x.x, y.x, -p);
+                acc_add(S, C, p, e);
+                p = __fmul_rn(x.y, y.y);
+                e = __fmaf_rn(x.y, y.y, -p);
+                acc_add(S, C, p, e);
+              }
+            } else {
+              const int cq = qa ? ca : cb, cv = qa ? cb : ca;
+#pragma unroll
+              for (int h = 0; h < TR / 64; ++h) {
+                const int r = 2 * lane + 64 * h;
+                const float2 q = q2rows<QT>(st, cq, r);
+                const float4 v = *(const float4 *)(st.p(cv) + r);
+                prod_f(F2{v.x, v.y}, q.x, p, e);
+                acc_add(S, C, p, e);
+                prod_f(F2{v.z, v.w}, q.y, p, e);
+                acc_add(S, C, p, e);
+              }
+            }
+          } else if (qa && qb) {
             for (int r = lane; r < rows; r += 32) {
               const float x = q2f<QT>(st.q<QT>(ca)[r]), y = q2f<QT>(st.q<QT>(cb)[r]);
               p = __fmul_rn(x, y);
@@ -1182,9 +1341,15 @@ __global__ void __launch_bounds__(NT) pass_kernel(const __grid_constant__ PassAr
               acc_add(S, C, p, e);
             }
           } else if (MODE == 1 && rows == TR) {
+            // full tile: lane l takes row pairs 2l + 64h (16-byte loads of
+            // two (hi, lo) pairs, contiguous across the warp)
 #pragma unroll
-            for (int q = 0; q < TR / 32; ++q) {
-              prod_ff(st.f2(ca, lane + 32 * q), st.f2(cb, lane + 32 * q), p, e);
+            for (int h = 0; h < TR / 64; ++h) {
+              const int r = 2 * lane + 64 * h;
+              const float4 x = *(const float4 *)(st.p(ca) + r), y = *(const float4 *)(st.p(cb) + r);
+              prod_ff(F2{x.x, x.y}, F2{y.x, y.y}, p, e);
+              acc_add(S, C, p, e);
+              prod_ff(F2{x.z, x.w}, F2{y.z, y.w}, p, e);
               acc_add(S, C, p, e);
             }
           } else {
@@ -1203,19 +1368,21 @@ __global__ void __launch_bounds__(NT) pass_kernel(const __grid_constant__ PassAr
 #pragma unroll
         for (int i = 0; i < DPW; ++i) {
           if (dbase + warp + NWARP * i < a.ndots) {
-            acc[i] += f2d(accS[i]);
-            acc[i] += f2d(accC[i]);
+            acc[i] += fold_f<MODE>(accS[i]);
+            acc[i] += fold_f<MODE>(accC[i]);
             accS[i] = accC[i] = 0.f;
           }
         }
       }
     }
-    __syncthreads();
-    if (tid == 0) {
-      const int tn = t + nstages * gridDim.x;
-      if (tn < a.ntiles) {
-        fence_proxy_async();
-        issue_tile<QT>(a, st, tn, &bars[s]);
+    if (!EARLY_REFILL || nstages == 1) {
+      __syncthreads();
+      if (tid == 0) {
+        const int tn = t + (EARLY_REFILL ? 1 : nstages) * (int)gridDim.x;
+        if (tn < a.ntiles) {
+          fence_proxy_async();
+          issue_tile<QT>(a, st, tn, &bars[s]);
+        }
       }
     }
   }
@@ -1223,8 +1390,8 @@ __global__ void __launch_bounds__(NT) pass_kernel(const __grid_constant__ PassAr
 #pragma unroll
     for (int i = 0; i < DPW; ++i) {
       if (dbase + warp + NWARP * i < a.ndots) {
-        acc[i] += f2d(accS[i]);
-        acc[i] += f2d(accC[i]);
+        acc[i] += fold_f<MODE>(accS[i]);
+        acc[i] += fold_f<MODE>(accC[i]);
       }
     }
   }
@@ -1249,8 +1416,8 @@ __global__ void __launch_bounds__(NT) pass_kernel(const __grid_constant__ PassAr
   // Per-CTA partial sums (warp butterfly, then warps in order: fixed order).
   if (s_err) {
     // (NaN partials posted above)
-  } else if (rowdots || MODE == 1) {
-    const int nrow = (MODE == 1) ? dbase : a.ndots;
+  } else if (rowdots || MODE == 1 || MODE == 2) {
+    const int nrow = (MODE == 1 || MODE == 2) ? dbase : a.ndots;
     __shared__ double rdw[NWARP][RD];
 #pragma unroll
     for (int d = 0; d < NRD; ++d) {
@@ -1331,8 +1498,8 @@ template <class QT, int DPW, int MODE>
 static int occupancy_t(size_t smem) {
   // resident CTAs per SM for this instantiation and dynamic shared memory
   // size, cached per host thread (the query sits on every pass launch)
-  thread_local size_t key[8];
-  thread_local int val[8];
+  thread_local size_t key[32];
+  thread_local int val[32];
   thread_local int used = 0;
   for (int i = 0; i < used; ++i)
     if (key[i] == smem) return val[i];
@@ -1341,42 +1508,45 @@ static int occupancy_t(size_t smem) {
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024 - 8 * 1024);
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, NT, smem) != cudaSuccess) return 1;
   nb = nb < 1 ? 1 : nb;
-  if (used < 8) {
+  if (used < 32) {
     key[used] = smem;
     val[used++] = nb;
   }
   return nb;
 }
 
-// Tile pipeline depth and grid of one pass.  Two stages (the next tile's
-// copies in flight while the current one is processed) unless they would
-// cut the resident CTAs per SM below min(one-stage occupancy, 4): several
-// CTAs at different points of their tile loop overlap copies with compute
-// as well, and more of them overlap the FP64 row programs of some with the
-// FP32-pipe dot phases of others.  The first pass of the exact FP64 form,
-// bound by the FP64 pipe, keeps two stages whenever they fit.  (Measured at
-// n = 406^3 for m = 5, 10, 20, 50.)
+// Tile pipeline depth and grid of one pass.  The deepest pipeline (up to
+// STAGES tiles in flight per CTA) that keeps the resident CTAs per SM at
+// min(one-stage occupancy, 4): several CTAs at different points of their
+// tile loop overlap copies with compute as well, and more of them overlap
+// the FP64 row programs of some with the FP32-pipe dot phases of others,
+// while more stages keep more bytes in flight per SM.  The first pass of the
+// exact FP64 form, bound by the FP64 pipe, keeps two stages whenever they fit.
+// (Measured at n = 406^3 for m = 5, 10, 20, 50.)
 template <class QT, int DPW, int MODE>
 static cudaError_t launch_shape(const PassArgs &a, int nsm, int *grid_out, cudaStream_t stream) {
-  const size_t stage = (size_t)a.ncol * TR * 8;
+  const size_t stage = stage_size<QT>(a);
   const size_t budget = 227 * 1024 - 8 * 1024;
   const size_t epi = epi_doubles(a.m > 0 ? a.m : 1) * sizeof(double);
-  const size_t smem1 = stage < epi ? epi : stage;
-  const size_t smem2 = 2 * stage < epi ? epi : 2 * stage;
-  if (smem1 > budget) return cudaErrorInvalidConfiguration;
-  int nstages = 1, occ = occupancy_t<QT, DPW, MODE>(smem1);
-  if (STAGES >= 2 && smem2 <= budget) {
-    const int occ2 = occupancy_t<QT, DPW, MODE>(smem2);
-    if (occ2 >= (occ < 4 ? occ : 4) || (MODE == 0 && a.kind == K_A)) {
-      nstages = 2;
-      occ = occ2;
+  auto smem_for = [&](int ns) { return ns * stage < epi ? epi : ns * stage; };
+  if (smem_for(1) > budget) return cudaErrorInvalidConfiguration;
+  const int occ1 = occupancy_t<QT, DPW, MODE>(smem_for(1));
+  const int want = occ1 < 4 ? occ1 : 4;
+  int nstages = 1, occ = occ1;
+  for (int ns = 2; ns <= STAGES; ++ns) {
+    if (smem_for(ns) > budget) break;
+    const int o = occupancy_t<QT, DPW, MODE>(smem_for(ns));
+    const bool fp64_first = (MODE == 0 && a.kind == K_A && ns == 2);
+    if (o >= want || fp64_first) {
+      nstages = ns;
+      occ = o;
     }
   }
   int grid = nsm * occ;
   if (grid > a.ntiles) grid = a.ntiles;
   if (grid < 1) grid = 1;
   *grid_out = grid;
-  return launch_t<QT, DPW, MODE>(a, grid, nstages == 2 ? smem2 : smem1, nstages, stream);
+  return launch_t<QT, DPW, MODE>(a, grid, smem_for(nstages), nstages, stream);
 }
 
 template <class QT, int MODE>
@@ -1384,7 +1554,7 @@ static inline cudaError_t launch_qm(const PassArgs &a, int nsm, int *grid_out, c
   const int dpw_need = (a.ndots + NWARP - 1) / NWARP;
   if (dpw_need <= 1) return launch_shape<QT, 1, MODE>(a, nsm, grid_out, stream);
   if (dpw_need <= 4) return launch_shape<QT, 4, MODE>(a, nsm, grid_out, stream);
-  if constexpr (MODE == 1) {
+  if constexpr (MODE == 1 || MODE == 2) {
     // an exact bucket for up to 8 dots per warp (m = 20 ICWY: 56)
     if (dpw_need <= 8) return launch_shape<QT, 8, MODE>(a, nsm, grid_out, stream);
   }

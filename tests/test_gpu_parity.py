@@ -278,7 +278,9 @@ def test_step_parity_fp32_dots_m20(aa, ora, orth):
 @pytest.mark.parametrize("orth", VARIANTS)
 @pytest.mark.parametrize("m", [20, 50])
 def test_qradd_fp32_dots_deep(aa, ora, orth, m):
-    """QR factors with FP32-pipe dot products after m + 6 adds, ragged n."""
+    """QR factors with FP32-pipe dot products after m + 6 adds, ragged n:
+    the exact form's tolerance, 1e-11 (DCGS-2 1e-9); measured at m = 20, 50,
+    64: R to 2.3e-15 relative, Q to 1.3e-16."""
     n = 4097
     V = aa_synth.uniform(80 + m, (m + 6) * n).reshape(m + 6, n)
     O = ora.Oracle(n, m, orth)
@@ -288,7 +290,7 @@ def test_qradd_fp32_dots_deep(aa, ora, orth, m):
         G.qradd(dev(V[j]))
     Qo, Ro, _ = O.get_qr()
     Qg, Rg, _ = G.get_qr()
-    tol = 1e-10 if orth != "dcgs2" else 1e-8
+    tol = 1e-11 if orth != "dcgs2" else 1e-9
     assert np.max(np.abs(Rg - Ro)) <= tol * np.abs(Ro).max(), orth
     assert np.max(np.abs(Qg - Qo)) <= tol, orth
 
@@ -384,7 +386,9 @@ def test_qradd_deep_history(aa, ora, orth, m):
     """QR factors after m + 6 adds (6 deletes) for the bench's history depths
     and the largest one the library takes (64), on a ragged n.  The inputs
     are well conditioned (independent uniform vectors), so the factors agree
-    to the same tolerance as at small m."""
+    to the same tolerance as at small m: 1e-11 (DCGS-2 1e-9), the bound that
+    holds at every m here (measured at m = 20, 50, 64: R to 3e-15 relative,
+    Q to 1.3e-16)."""
     n = 4097
     V = aa_synth.uniform(70 + m, (m + 6) * n).reshape(m + 6, n)
     O = ora.Oracle(n, m, orth)
@@ -394,7 +398,7 @@ def test_qradd_deep_history(aa, ora, orth, m):
         G.qradd(dev(V[j]))
     Qo, Ro, _ = O.get_qr()
     Qg, Rg, _ = G.get_qr()
-    tol = 1e-10 if orth != "dcgs2" else 1e-8
+    tol = 1e-11 if orth != "dcgs2" else 1e-9
     assert np.max(np.abs(Rg - Ro)) <= tol * np.abs(Ro).max(), orth
     assert np.max(np.abs(Qg - Qo)) <= tol, orth
     if orth != "dcgs2":  # the literal DCGS-2 update is checked against the oracle only
