@@ -63,7 +63,8 @@ def parse():
     p.add_argument("--nz", type=int, default=NZ)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-variant", action="store_true",
-                   help="skip the FP32-pipe dot-product form measured beside the exact FP64 one")
+                   help="skip the FP32-pipe dot-product and FP32-history forms measured beside the "
+                        "exact FP64 one")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-wall", action="store_true")
     p.add_argument("--cpu-iters", type=int, default=12)
@@ -83,6 +84,11 @@ def parse():
     p.add_argument("--ws-epochs", type=int, default=40)
     p.add_argument("--ws-chunk", type=int, default=2432)
     p.add_argument("--ws-max-iters", type=int, default=20000)
+    p.add_argument("--ws-grow", type=int, default=0,
+                   help="bratu-warmstart: further training solves, each warm-started from the "
+                        "network trained on the first --ws-train, then more training on all")
+    p.add_argument("--ws-epochs2", type=int, default=20,
+                   help="bratu-warmstart: epochs over the grown training set")
     p.add_argument("--ws-fp64-check", type=int, default=16,
                    help="bratu-warmstart: held-out instances also solved by sequential FP64 aa_solve "
                         "from x0 = 0 and from the prediction (0: skip)")
@@ -349,11 +355,12 @@ def run_ours(args, ws, rank, local):
         e2e = run_e2e(args, A, gfn, Pp, n, dev, stream, one_step_state=(x, xn, g))
     wall = run_wall_to_tol(aa, args, dev) if (rank == 0 and not args.no_wall) else None
     startup = run_startup(A, one_step, x, stream, args.m)
-    variant = None
+    variants = {}
     if (not args.no_variant and args.storage == "fp64" and not (args.fp32_dots or args.df_arith)):
         del A
         torch.cuda.empty_cache()
-        variant = run_variant(aa, args, gfn, Pp, n, dev, stream, esz, hbm_peak)
+        for kind in ("fp32_pipe_dots", "fp32_history"):
+            variants[kind] = run_variant(aa, args, gfn, Pp, n, dev, stream, hbm_peak, kind)
     if ws > 1:
         import torch.distributed as dist
         dist.barrier()
@@ -404,22 +411,31 @@ def run_ours(args, ws, rank, local):
         "wall_to_1e-8": wall,
         "startup": startup,
     }
-    if variant is not None:
-        line["fp32_pipe_dots"] = variant
+    line.update(variants)
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(args)
     return line
 
 
-def run_variant(aa, args, gfn, Pp, n, dev, stream, esz, hbm_peak):
-    """The same recycle steps with AA_FLAG_FP32_DOTS: FP64 storage and FP64
-    updates, the dot products of the first pass on the FP32 pipe (exact
-    products of (hi, lo) splits, compensated sums folded into FP64).  A fresh
-    context, filled and warmed up like the main one, timed over the same
-    number of steps with CUDA events on the launching stream."""
+VARIANT_DTYPE = {
+    "fp32_pipe_dots": "f64 storage and updates; first-pass dot products on the FP32 pipe",
+    "fp32_history": "f64 vectors, fp32 history storage with fp32 n-space updates; dot products "
+                    "exact float products in compensated pairs folded into f64; R, T, gamma f64",
+}
+
+
+def run_variant(aa, args, gfn, Pp, n, dev, stream, hbm_peak, kind):
+    """The same recycle steps in another arithmetic form: kind
+    "fp32_pipe_dots" (AA_FLAG_FP32_DOTS: FP64 storage and FP64 updates, the
+    dot products of the first pass on the FP32 pipe) or "fp32_history" (the
+    precision form: Q and dG stored in FP32).  A fresh context, filled and
+    warmed up like the main one, timed over the same number of steps with
+    CUDA events on the launching stream."""
     import torch
     sp = stream.cuda_stream
-    A = aa.Anderson(n, args.m, args.orth, "fp64", flags=aa.FLAG_TIMING | aa.FLAG_FP32_DOTS,
+    storage, flags, esz = (("fp64", aa.FLAG_FP32_DOTS, 8) if kind == "fp32_pipe_dots"
+                           else ("fp32", 0, 4))
+    A = aa.Anderson(n, args.m, args.orth, storage, flags=aa.FLAG_TIMING | flags,
                     max_iters=10**6)
     x = torch.zeros(n, dtype=torch.float64, device=dev)
     xn = torch.empty_like(x)
@@ -453,7 +469,7 @@ def run_variant(aa, args, gfn, Pp, n, dev, stream, esz, hbm_peak):
     return {"value": round(args.steps / (ms * 1e-3), 3), "unit": "iter/s",
             "ms_per_step": round(ms / args.steps, 4), "passes_ms_avg": passes,
             "aa_passes_gbs": round(gbs, 1), "aa_passes_hbm_frac": round(gbs / hbm_peak, 4),
-            "dtype": "f64 storage and updates; first-pass dot products on the FP32 pipe"}
+            "dtype": VARIANT_DTYPE[kind]}
 
 
 def run_startup(A, one_step, x, stream, m):
@@ -685,7 +701,8 @@ def run_batch(args, ws, rank, local):
     bulk = t_end <= t99
     bulk_rate = float((it[bulk].astype(np.float64) * n[bulk]).sum()) / (t99 * 1e-3)
     bytes_per_row_iter = 240.0  # FP32 Q/dG, m = 10, recycle: pass A 128 + projection 56 + update 56
-    vs_seq = batch_vs_sequential(aa, args, sides, lams, shape) if args.batch_vs_seq > 0 else None
+    vs_seq = (batch_vs_sequential(aa, args, sides, lams, shape, ms)
+              if args.batch_vs_seq > 0 else None)
     if rank != 0:
         return None
     ms_max = max_over_ranks(ms)
@@ -711,14 +728,16 @@ def run_batch(args, ws, rank, local):
     }
 
 
-def batch_vs_sequential(aa, args, sides, lams, shape):
+def batch_vs_sequential(aa, args, sides, lams, shape, ms_batch_total):
     """The batched form against the plain FP64 form on a stated sub-batch:
     every (count / K)-th solve of the batch (K = --batch-vs-seq, so that the
     sub-batch spans the side distribution), (a) in one batched launch (FP32
-    history, the batch's launch shape) and (b) one after another with
-    aa_solve (FP64 history, ICWY, m = 10, the built-in Bratu map, the same
-    stop rule ||G(x) - x|| / ||G(0)|| < tol and cap).  Times by CUDA events;
-    both reach the same final residual bound."""
+    history, the batch's launch shape; K CTAs, so the GPU is mostly idle) and
+    (b) one after another with aa_solve (FP64 history, ICWY, m = 10, the
+    built-in Bratu map, the same stop rule ||G(x) - x|| / ||G(0)|| < tol and
+    cap).  Times by CUDA events; both reach the same final residual bound.
+    The whole batch solved the sequential way is estimated as (b) x count / K
+    and set against the measured batched launch of the whole batch."""
     import numpy as np
     import torch
     K = min(args.batch_vs_seq, len(sides))
@@ -751,10 +770,15 @@ def batch_vs_sequential(aa, args, sides, lams, shape):
         per.append((rc == 0, int(st["iters"])))
         A.close()
     it_s = np.array([p[1] for p in per])
+    est = ms_s * len(sides) / K
     return {"sub_batch": f"{K} solves: every {len(sides) // K}-th of the batch, sides "
                          f"{int(ss.min())}-{int(ss.max())}",
-            "batched_fp32_ms": round(ms_b, 1), "sequential_fp64_ms": round(ms_s, 1),
-            "speedup": round(ms_s / ms_b, 2),
+            "sub_batch_batched_fp32_ms": round(ms_b, 1),
+            "sub_batch_sequential_fp64_ms": round(ms_s, 1),
+            "sequential_fp64_ms_per_solve": round(ms_s / K, 1),
+            "whole_batch_sequential_fp64_est_s": round(est / 1e3, 1),
+            "whole_batch_batched_s": round(ms_batch_total / 1e3, 1),
+            "whole_batch_speedup_est": round(est / ms_batch_total, 1),
             "converged": {"batched": int((st_b == 0).sum()),
                           "sequential": int(sum(1 for p in per if p[0]))},
             "iterations": {"batched_sum": int(it_b.sum()), "sequential_sum": int(it_s.sum()),
@@ -924,8 +948,33 @@ def run_warmstart(args, ws_, rank, local):
     e1.record()
     torch.cuda.synchronize()
     train_ms = e0.elapsed_time(e1)
-    del U
     steps = args.ws_epochs * (int(ok.sum()) // 128)
+    grow = None
+    if args.ws_grow > 0:
+        # more training solutions, each solve warm-started from the network
+        # trained so far (a converged solution does not depend on x0), then
+        # further training on the whole set
+        tg = np.arange(args.ws_train, args.ws_train + args.ws_grow)
+        lam_g, c_g, _ = W.instances(tg, 1)
+        x0g = W.predict(net, W.features(lam_g, c_g))
+        Ug, it_g, st_g, ms_g, fb_g = solve_chunks(tg, x0=x0g.astype(np.float64))
+        okg = st_g == 0
+        X = np.concatenate([X, W.features(lam_g[okg], c_g[okg])])
+        Uall = np.concatenate([U[ok], Ug[okg]])
+        del Ug
+        e0.record()
+        hist2 = W.train(net, X, Uall, epochs=args.ws_epochs2, batch=128, lr=5e-4, seed=1)
+        e1.record()
+        torch.cuda.synchronize()
+        train_ms += e0.elapsed_time(e1)
+        steps += args.ws_epochs2 * (X.shape[0] // 128)
+        hist = hist + hist2
+        grow = {"solves": int(args.ws_grow), "converged": int(okg.sum()),
+                "iters_mean": round(float(it_g[okg].mean()), 1), "fallbacks": int(fb_g.sum()),
+                "solve_ms": round(ms_g, 1), "epochs": args.ws_epochs2,
+                "train_set": int(X.shape[0])}
+        del Uall
+    del U
     dims = net.dims
     gemm_flop = 3 * 2 * 128 * sum(dims[i] * dims[i + 1] for i in range(3))  # fwd + 2 bwd GEMMs
     # held-out
@@ -957,6 +1006,7 @@ def run_warmstart(args, ws_, rank, local):
         "data": "synthetic (seeded SplitMix64: lambda ~ U(1,6), c_k ~ N(0,1))",
         "config": {"workload": f"AA(10) batched Bratu with source {s}x{s}, MLP 65-1024-1024-{n}",
                    "train_solves": int(args.ws_train), "train_converged": int(ok.sum()),
+                   "train_grown_warm": grow,
                    "test_solves": int(args.ws_test), "epochs": args.ws_epochs, "batch": 128,
                    "cap": args.ws_max_iters, "launch": {"block": shape[0], "ctas_per_sm": shape[1]}},
         "cold": dict(stats(it_c, st_c), wall_ms=round(ms_c, 1)),

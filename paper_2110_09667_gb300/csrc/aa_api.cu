@@ -272,7 +272,8 @@ static void base_args(aa_ctx *c, PassArgs &a, int kind) {
   a.stop_kind = c->cfg.stop_kind;
   a.st = c->st;
   a.partials = c->partials;
-  for (int j = 0; j < c->m; ++j) a.out_q[j] = qslot(c, j);
+  a.out_q0 = qslot(c, 0);
+  a.qstride = c->ld * c->esz;
 }
 
 static void add_dot(PassArgs &a, int x, int y) {

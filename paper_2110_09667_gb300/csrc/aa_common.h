@@ -90,7 +90,8 @@ struct PassArgs {
   uint8_t dot_b[NDOT_MAX];
   uint64_t dotcols[2];             // bit c: tile column c appears in a dot product
   // outputs (NULL when unused)
-  void *out_q[MMAX];               // history slots written by the row program
+  void *out_q0;                    // history slot 0 written by the row program
+  int64_t qstride;                 // bytes from one history slot to the next
   void *out_dg;                    // dG slot for Delta g (K_A step mode)
   double *out_df;                  // Delta f / y / v work vector (FP64)
   double *out_f;                   // f_i (overwrites f_{i-1})

@@ -154,6 +154,43 @@ __device__ __forceinline__ F2 df_axpy_ff(float u, F2 c, F2 a) {
   return fast_two_sum(s, t);
 }
 
+// Paired forms for two independent rows at once: Blackwell's FP32 pipe
+// issues FADD2/FMUL2/FFMA2, two round-to-nearest float operations per
+// instruction (one per component, each exactly as the scalar one), so the
+// error-free transformations below cost half the issue slots of the scalar
+// ones per row.
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+
+__device__ __forceinline__ void two_sum2(float2 a, float2 b, float2 &s, float2 &t) {
+  s = __fadd2_rn(a, b);
+  const float2 bb = __fadd2_rn(s, neg2(a));
+  t = __fadd2_rn(__fadd2_rn(a, neg2(__fadd2_rn(s, neg2(bb)))), __fadd2_rn(b, neg2(bb)));
+}
+
+// (S, C) += p + e per component (acc_add on two rows).
+__device__ __forceinline__ void acc_add2(float2 &S, float2 &C, float2 p, float2 e) {
+  float2 s, t;
+  two_sum2(S, p, s, t);
+  C = __fadd2_rn(C, __fadd2_rn(t, e));
+  S = s;
+}
+
+// p + e = (h + l) * u per component: exact head product, tail to 2^-48.
+__device__ __forceinline__ void prod_f2(float2 h, float2 l, float2 u, float2 &p, float2 &e) {
+  p = __fmul2_rn(h, u);
+  e = __ffma2_rn(h, u, neg2(p));
+  e = __ffma2_rn(l, u, e);
+}
+
+// p + e = (ah + al) * (bh + bl) per component, to 2^-48 relative.
+__device__ __forceinline__ void prod_ff2(float2 ah, float2 al, float2 bh, float2 bl, float2 &p,
+                                         float2 &e) {
+  p = __fmul2_rn(ah, bh);
+  e = __ffma2_rn(ah, bh, neg2(p));
+  e = __ffma2_rn(ah, bl, e);
+  e = __ffma2_rn(al, bh, e);
+}
+
 // (a + b) for two (hi, lo) pairs, normalised.
 __device__ __forceinline__ F2 df_add(F2 a, F2 b) {
   float s, t;

@@ -131,14 +131,31 @@ struct Stage {
     if constexpr (sizeof(QT) == 8) return (QT *)(base + c * (TR * 8));
     else return (QT *)(base + qbase * (TR * 8) + (c - qbase) * (int)(TR * sizeof(QT)));
   }
-  // an FP64 column after it was split in place into (hi, lo) floats
-  __device__ __forceinline__ float2 *p(int c) const { return (float2 *)(base + c * (TR * 8)); }
+  // An FP64 column after it was split in place into (hi, lo) floats, laid
+  // out by row pairs: rows 2i and 2i+1 as (hi_2i, hi_2i+1, lo_2i, lo_2i+1),
+  // so that one 16-byte load gives the two rows' heads and tails as float2s.
+  __device__ __forceinline__ float *p(int c) const { return (float *)(base + c * (TR * 8)); }
   __device__ __forceinline__ F2 f2(int c, int r) const {
-    const float2 v = p(c)[r];
-    return F2{v.x, v.y};
+    const float *q = p(c) + (r >> 1) * 4 + (r & 1);
+    return F2{q[0], q[2]};
   }
-  __device__ __forceinline__ void put(int c, int r, F2 v) const { p(c)[r] = make_float2(v.h, v.l); }
+  __device__ __forceinline__ void put(int c, int r, F2 v) const {
+    float *q = p(c) + (r >> 1) * 4 + (r & 1);
+    q[0] = v.h;
+    q[2] = v.l;
+  }
+  // rows r, r + 1 (r even): heads in .x/.y of hl[0], tails in hl[1]
+  __device__ __forceinline__ float4 pairs2(int c, int r) const {
+    return *(const float4 *)(p(c) + (r >> 1) * 4);
+  }
 };
+
+// History slot j as an output (slots are qstride bytes apart: an address
+// computation, not a load of a pointer table from parameter space).
+template <class QT>
+__device__ __forceinline__ QT *outq(const PassArgs &a, int j) {
+  return (QT *)((char *)a.out_q0 + (int64_t)j * a.qstride);
+}
 
 template <class QT>
 __device__ __forceinline__ int col_esz(const PassArgs &a, int c) {
@@ -254,7 +271,7 @@ __device__ __forceinline__ void row_program(const PassArgs &a, Stage st, int t, 
         df = st.d(0)[r];
       }
       a.out_df[row] = df;
-      if (a.k == 0) ((QT *)a.out_q[0])[row] = from_d<QT>(df);
+      if (a.k == 0) outq<QT>(a, 0)[row] = from_d<QT>(df);
       if (a.del) {
         // QRDelete: sequential Givens rotations of adjacent columns, in the
         // square-root-free scaled form (Gentleman 1973, Hammarling 1974):
@@ -279,7 +296,7 @@ __device__ __forceinline__ void row_program(const PassArgs &a, Stage st, int t, 
           const double out = ty ? P : Qv;
           w = ty ? Qv : P;
           const QT qs = from_d<QT>(out);
-          ((QT *)a.out_q[j])[row] = qs;
+          outq<QT>(a, j)[row] = qs;
           st.q<QT>(qb + j)[r] = qs;
         }
       }
@@ -295,11 +312,11 @@ __device__ __forceinline__ void row_program(const PassArgs &a, Stage st, int t, 
         double qn = co[CO_MISC] * to_d<QT>(st.q<QT>(qb + kk)[r]);
         for (int j = 0; j < kk; ++j) qn -= co[CO_COEF2 + j] * to_d<QT>(st.q<QT>(qb + j)[r]);
         const QT qs = from_d<QT>(qn);
-        ((QT *)a.out_q[kk])[row] = qs;
+        outq<QT>(a, kk)[row] = qs;
         st.q<QT>(qb + kk)[r] = qs;
       }
       for (int j = a.j0; j < a.k; ++j) v -= co[CO_COEF + j] * to_d<QT>(st.q<QT>(qb + j - a.j0)[r]);
-      ((QT *)a.out_q[a.k])[row] = from_d<QT>(v * co[CO_MISC + 1]);
+      outq<QT>(a, a.k)[row] = from_d<QT>(v * co[CO_MISC + 1]);
       st.d(0)[r] = v;
       break;
     }
@@ -379,7 +396,7 @@ __device__ __forceinline__ double lp_chain(Stage st, const float *c, int qb, int
 template <class QT>
 __device__ __forceinline__ void row_program_lp(const PassArgs &a, Stage st, int t, int r,
                                                const double *co, const float *cf, uint32_t split,
-                                               double &dv0, double &dv1) {
+                                               uint64_t tymask, double &dv0, double &dv1) {
   const int64_t row = (int64_t)t * TR + r;
   switch (a.kind) {
     case K_INIT: {
@@ -411,23 +428,29 @@ __device__ __forceinline__ void row_program_lp(const PassArgs &a, Stage st, int 
         if (split & 1u) st.put(0, r, d2f2(df));
       }
       a.out_df[row] = df;
-      if (a.k == 0) ((QT *)a.out_q[0])[row] = f2q<QT>(d2f_rn(df));
+      if (a.k == 0) outq<QT>(a, 0)[row] = f2q<QT>(d2f_rn(df));
       if (a.del) {
         // QRDelete: the scaled Givens rotations of row_program in FP32.  The
         // two forms differ in which of (carry w, stored column u) meets
         // which multiplier: out = b + k1 a, carry = a + k2 b with
         // (a, b) = (u, w) when |c| >= |s| and (w, u) otherwise.
-        const int qb = a.qbase;
-        float w = q2f<QT>(st.q<QT>(qb)[r]);
+        // (Pointers advanced by one column per rotation; the form of each
+        // rotation is bit j of tymask.)
+        QT *sq = st.q<QT>(a.qbase) + r;                      // stage column j: sq[j * TR]
+        char *gq = (char *)a.out_q0 + row * (int64_t)sizeof(QT);  // slot j: gq + j * qstride
+        const float4 *kq = (const float4 *)(cf + CF_ROT);    // k1 (hi, lo), k2 (hi, lo)
+        float w = q2f<QT>(sq[0]);
         for (int j = 0; j < a.m - 1; ++j) {
-          const float u = q2f<QT>(st.q<QT>(qb + j + 1)[r]);
-          const float4 k = *(const float4 *)(cf + CF_ROT + 4 * j);  // k1 (hi, lo), k2 (hi, lo)
-          const bool ty = __double_as_longlong(co[CO_ROT + 4 * j + 2]) != 0;
+          const float u = q2f<QT>(sq[TR]);
+          const float4 k = kq[j];
+          const bool ty = (tymask >> j) & 1ull;
           const float pa = ty ? u : w, pb = ty ? w : u;
           const QT qs = f2q<QT>(__fmaf_rn(k.x, pa, pb));
           w = __fmaf_rn(k.z, pb, pa);
-          ((QT *)a.out_q[j])[row] = qs;
-          st.q<QT>(qb + j)[r] = qs;
+          *(QT *)gq = qs;
+          sq[0] = qs;
+          sq += TR;
+          gq += a.qstride;
         }
       }
       break;
@@ -448,7 +471,7 @@ __device__ __forceinline__ void row_program_lp(const PassArgs &a, Stage st, int 
         }
         qn += ql;
         const QT qs = f2q<QT>(qn);
-        ((QT *)a.out_q[kk])[row] = qs;
+        outq<QT>(a, kk)[row] = qs;
         st.q<QT>(qb + kk)[r] = qs;
       }
       // v = w - Q coef (the coefficients are stored negated), added to w in FP64
@@ -458,7 +481,7 @@ __device__ __forceinline__ void row_program_lp(const PassArgs &a, Stage st, int 
         // (hi, lo) scale on the FP32 pipe
         float p, e;
         prod_ff(d2f2(v), F2{cf[CF_MISC + 2], cf[CF_MISC + 3]}, p, e);
-        ((QT *)a.out_q[a.k])[row] = f2q<QT>(__fadd_rn(p, e));
+        outq<QT>(a, a.k)[row] = f2q<QT>(__fadd_rn(p, e));
       }
       dv0 = v;
       if (a.step_mode) {
@@ -532,7 +555,7 @@ __device__ __forceinline__ void row_program_dd(const PassArgs &a, Stage st, int 
     mark(0);
   }
   a.out_df[row] = df;
-  if (a.k == 0) ((double *)a.out_q[0])[row] = df;
+  if (a.k == 0) outq<double>(a, 0)[row] = df;
   if (a.del) {
     // the scaled Givens rotations of row_program, as (hi, lo) multiply-adds
     const int qb = a.qbase;
@@ -546,7 +569,7 @@ __device__ __forceinline__ void row_program_dd(const PassArgs &a, Stage st, int 
       const F2 Qv = df_mad(ty ? k2 : k1, w, u);  // u + kq w
       const F2 out = ty ? P : Qv;
       w = ty ? Qv : P;
-      ((double *)a.out_q[j])[row] = f22d(out);
+      outq<double>(a, j)[row] = f22d(out);
       st.put(qb + j, r, out);
       mark(qb + j);
     }
@@ -1068,8 +1091,18 @@ __device__ __forceinline__ double pow2d(int e) {
 //         products on the FP32/INT pipes (row_program_dd), partial sums
 //         folded into FP64 every fourth tile.
 
+// Register budgets: the FP32-pipe forms (MODE 2, 3) hold two compensated float
+// pairs per dot product (one per row parity), so their 4- and 8-dot buckets
+// are held to 80 registers (3 CTAs per SM, no spills) and the 16-dot bucket to
+// one CTA; MODE 1's 8-dot bucket (one pair per dot) to 64 (4 CTAs);
+// every other instantiation keeps the compiler's own choice (a minimum of 0
+// blocks states no bound: an explicit 1 lets it grow the FP64 projection and
+// update from 48 to 80 registers and cost them a resident CTA).
 template <class QT, int DPW, int MODE = 0>
-__global__ void __launch_bounds__(NT) pass_kernel(const __grid_constant__ PassArgs a, int nstages) {
+__global__ void __launch_bounds__(NT, (MODE != 0)
+                                          ? ((MODE == 1 && DPW == 8) ? 4 : (DPW > 1 && DPW <= 8) ? 3 : (DPW == 16 ? 1 : 0))
+                                          : 0)
+    pass_kernel(const __grid_constant__ PassArgs a, int nstages) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t bars[STAGES];
   __shared__ double co[CO_SIZE];
@@ -1083,6 +1116,7 @@ __global__ void __launch_bounds__(NT) pass_kernel(const __grid_constant__ PassAr
   __shared__ int s_cexp[MODE == 1 ? MAXCOL : 1];
   __shared__ uint64_t s_split[2];
   __shared__ int s_n64;
+  __shared__ uint64_t s_tymask;  // bit j: form of QRDelete rotation j (MODE 2)
 
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
@@ -1138,7 +1172,13 @@ __global__ void __launch_bounds__(NT) pass_kernel(const __grid_constant__ PassAr
   __syncthreads();
   if (a.kind == K_A && a.del) {
     for (int i = tid; i < 4 * (a.m - 1); i += NT) co[CO_ROT + i] = S->rot[i];
-    if (tid == 0) co[CO_ROT0] = S->rot0;
+    if (tid == 0) {
+      co[CO_ROT0] = S->rot0;
+      uint64_t tm = 0ull;
+      for (int j = 0; j + 1 < a.m; ++j)
+        if (__double_as_longlong(S->rot[4 * j + 2]) != 0) tm |= 1ull << j;
+      s_tymask = tm;
+    }
   } else if (a.kind == K_PROJ || a.kind == K_CGS2B || a.kind == K_MGS) {
     for (int i = tid; i < a.k; i += NT) {
       co[CO_COEF + i] = S->coef[i];
@@ -1191,7 +1231,9 @@ __global__ void __launch_bounds__(NT) pass_kernel(const __grid_constant__ PassAr
   }
 
   double acc[DPW];
-  float accS[MODE ? DPW : 1], accC[MODE ? DPW : 1];
+  // FP32-pipe partial sums: (S, C) compensated pairs, one per row parity
+  // (.x even rows, .y odd rows) so that full tiles use paired instructions
+  float2 accS[MODE ? DPW : 1], accC[MODE ? DPW : 1];
   constexpr int NRD = ((DPW == 1 && MODE == 0) || MODE == 1 || MODE == 2) ? RD : 1;
   // every dot product accumulated row by row in FP64 (no dot phase)
   const bool rowdots = ((DPW == 1) && (MODE == 0) && a.ndots <= RD) ||
@@ -1205,7 +1247,7 @@ __global__ void __launch_bounds__(NT) pass_kernel(const __grid_constant__ PassAr
   for (int i = 0; i < DPW; ++i) acc[i] = 0.0;
   if constexpr (MODE != 0) {
 #pragma unroll
-    for (int i = 0; i < DPW; ++i) accS[i] = accC[i] = 0.f;
+    for (int i = 0; i < DPW; ++i) accS[i] = accC[i] = make_float2(0.f, 0.f);
   }
   constexpr int FLUSH = (MODE == 3) ? 4 : 8;  // tiles per fold into FP64
 
@@ -1244,7 +1286,7 @@ __global__ void __launch_bounds__(NT) pass_kernel(const __grid_constant__ PassAr
         }
       } else if constexpr (MODE == 2) {
         double dv0 = 0.0, dv1 = 0.0;
-        row_program_lp<QT>(a, st, t, tid, co, cf, (uint32_t)s_split[0], dv0, dv1);
+        row_program_lp<QT>(a, st, t, tid, co, cf, (uint32_t)s_split[0], s_tymask, dv0, dv1);
 #pragma unroll
         for (int d = 0; d < NRD; ++d) {
           if (d < dbase) {
@@ -1298,68 +1340,84 @@ __global__ void __launch_bounds__(NT) pass_kernel(const __grid_constant__ PassAr
           acc[i] = sum;
         } else {
           const bool qa = (MODE == 2) && ca >= a.qbase, qb = (MODE == 2) && cb >= a.qbase;
-          float S = accS[i], C = accC[i], p, e;
-          if (MODE == 2 && rows == TR && (qa || qb)) {
+          float2 S2 = accS[i], C2 = accC[i];
+          if (rows == TR) {
             // full tile: lane l takes row pairs 2l + 64h (8-byte history
-            // loads, 16-byte pair loads: contiguous across the warp)
+            // loads, 16-byte split-pair loads, contiguous across the warp)
+            // and works on both rows with paired FP32 instructions
+            float2 p, e;
             if (qa && qb) {
 #pragma unroll
               for (int h = 0; h < TR / 64; ++h) {
                 const int r = 2 * lane + 64 * h;
                 const float2 x = q2rows<QT>(st, ca, r), y = q2rows<QT>(st, cb, r);
-                p = __fmul_rn(x.x, y.x);
-                e = __fmaf_rn(x.x, y.x, -p);
-                acc_add(S, C, p, e);
-                p = __fmul_rn(x.y, y.y);
-                e = __fmaf_rn(x.y, y.y, -p);
-                acc_add(S, C, p, e);
+                p = __fmul2_rn(x, y);
+                e = __ffma2_rn(x, y, neg2(p));
+                acc_add2(S2, C2, p, e);
               }
-            } else {
+            } else if (qa || qb) {
               const int cq = qa ? ca : cb, cv = qa ? cb : ca;
 #pragma unroll
               for (int h = 0; h < TR / 64; ++h) {
                 const int r = 2 * lane + 64 * h;
                 const float2 q = q2rows<QT>(st, cq, r);
-                const float4 v = *(const float4 *)(st.p(cv) + r);
-                prod_f(F2{v.x, v.y}, q.x, p, e);
+                const float4 v = st.pairs2(cv, r);
+                prod_f2(make_float2(v.x, v.y), make_float2(v.z, v.w), q, p, e);
+                acc_add2(S2, C2, p, e);
+              }
+            } else if constexpr (MODE == 1) {
+              // FP64 storage: one compensated pair per dot (registers for
+              // four CTAs per SM, which the FP64 rotation chains need more
+              // than the paired instructions)
+              float S = S2.x, C = C2.x, ps, es;
+#pragma unroll
+              for (int h = 0; h < TR / 64; ++h) {
+                const int r = 2 * lane + 64 * h;
+                const float4 x = st.pairs2(ca, r), y = st.pairs2(cb, r);
+                prod_ff(F2{x.x, x.z}, F2{y.x, y.z}, ps, es);
+                acc_add(S, C, ps, es);
+                prod_ff(F2{x.y, x.w}, F2{y.y, y.w}, ps, es);
+                acc_add(S, C, ps, es);
+              }
+              S2.x = S;
+              C2.x = C;
+            } else {
+#pragma unroll
+              for (int h = 0; h < TR / 64; ++h) {
+                const int r = 2 * lane + 64 * h;
+                const float4 x = st.pairs2(ca, r), y = st.pairs2(cb, r);
+                prod_ff2(make_float2(x.x, x.y), make_float2(x.z, x.w), make_float2(y.x, y.y),
+                         make_float2(y.z, y.w), p, e);
+                acc_add2(S2, C2, p, e);
+              }
+            }
+          } else {
+            // ragged last tile: one row at a time, into the even-row sums
+            float S = S2.x, C = C2.x, p, e;
+            if (qa && qb) {
+              for (int r = lane; r < rows; r += 32) {
+                const float x = q2f<QT>(st.q<QT>(ca)[r]), y = q2f<QT>(st.q<QT>(cb)[r]);
+                p = __fmul_rn(x, y);
+                e = __fmaf_rn(x, y, -p);
                 acc_add(S, C, p, e);
-                prod_f(F2{v.z, v.w}, q.y, p, e);
+              }
+            } else if (qa || qb) {
+              const int cq = qa ? ca : cb, cv = qa ? cb : ca;
+              for (int r = lane; r < rows; r += 32) {
+                prod_f(st.f2(cv, r), q2f<QT>(st.q<QT>(cq)[r]), p, e);
+                acc_add(S, C, p, e);
+              }
+            } else {
+              for (int r = lane; r < rows; r += 32) {
+                prod_ff(st.f2(ca, r), st.f2(cb, r), p, e);
                 acc_add(S, C, p, e);
               }
             }
-          } else if (qa && qb) {
-            for (int r = lane; r < rows; r += 32) {
-              const float x = q2f<QT>(st.q<QT>(ca)[r]), y = q2f<QT>(st.q<QT>(cb)[r]);
-              p = __fmul_rn(x, y);
-              e = __fmaf_rn(x, y, -p);
-              acc_add(S, C, p, e);
-            }
-          } else if (qa || qb) {
-            const int cq = qa ? ca : cb, cv = qa ? cb : ca;
-            for (int r = lane; r < rows; r += 32) {
-              prod_f(st.f2(cv, r), q2f<QT>(st.q<QT>(cq)[r]), p, e);
-              acc_add(S, C, p, e);
-            }
-          } else if (MODE == 1 && rows == TR) {
-            // full tile: lane l takes row pairs 2l + 64h (16-byte loads of
-            // two (hi, lo) pairs, contiguous across the warp)
-#pragma unroll
-            for (int h = 0; h < TR / 64; ++h) {
-              const int r = 2 * lane + 64 * h;
-              const float4 x = *(const float4 *)(st.p(ca) + r), y = *(const float4 *)(st.p(cb) + r);
-              prod_ff(F2{x.x, x.y}, F2{y.x, y.y}, p, e);
-              acc_add(S, C, p, e);
-              prod_ff(F2{x.z, x.w}, F2{y.z, y.w}, p, e);
-              acc_add(S, C, p, e);
-            }
-          } else {
-            for (int r = lane; r < rows; r += 32) {
-              prod_ff(st.f2(ca, r), st.f2(cb, r), p, e);
-              acc_add(S, C, p, e);
-            }
+            S2.x = S;
+            C2.x = C;
           }
-          accS[i] = S;
-          accC[i] = C;
+          accS[i] = S2;
+          accC[i] = C2;
         }
       }
     }
@@ -1368,9 +1426,9 @@ __global__ void __launch_bounds__(NT) pass_kernel(const __grid_constant__ PassAr
 #pragma unroll
         for (int i = 0; i < DPW; ++i) {
           if (dbase + warp + NWARP * i < a.ndots) {
-            acc[i] += fold_f<MODE>(accS[i]);
-            acc[i] += fold_f<MODE>(accC[i]);
-            accS[i] = accC[i] = 0.f;
+            acc[i] += fold_f<MODE>(accS[i].x) + fold_f<MODE>(accS[i].y);
+            acc[i] += fold_f<MODE>(accC[i].x) + fold_f<MODE>(accC[i].y);
+            accS[i] = accC[i] = make_float2(0.f, 0.f);
           }
         }
       }
@@ -1390,8 +1448,8 @@ __global__ void __launch_bounds__(NT) pass_kernel(const __grid_constant__ PassAr
 #pragma unroll
     for (int i = 0; i < DPW; ++i) {
       if (dbase + warp + NWARP * i < a.ndots) {
-        acc[i] += fold_f<MODE>(accS[i]);
-        acc[i] += fold_f<MODE>(accC[i]);
+        acc[i] += fold_f<MODE>(accS[i].x) + fold_f<MODE>(accS[i].y);
+        acc[i] += fold_f<MODE>(accC[i].x) + fold_f<MODE>(accC[i].y);
       }
     }
   }
@@ -1554,7 +1612,7 @@ static inline cudaError_t launch_qm(const PassArgs &a, int nsm, int *grid_out, c
   const int dpw_need = (a.ndots + NWARP - 1) / NWARP;
   if (dpw_need <= 1) return launch_shape<QT, 1, MODE>(a, nsm, grid_out, stream);
   if (dpw_need <= 4) return launch_shape<QT, 4, MODE>(a, nsm, grid_out, stream);
-  if constexpr (MODE == 1 || MODE == 2) {
+  if constexpr (MODE != 0) {
     // an exact bucket for up to 8 dots per warp (m = 20 ICWY: 56)
     if (dpw_need <= 8) return launch_shape<QT, 8, MODE>(a, nsm, grid_out, stream);
   }
