@@ -69,10 +69,11 @@ def parse():
     p.add_argument("--no-wall", action="store_true")
     p.add_argument("--cpu-iters", type=int, default=12)
     p.add_argument("--workload", default="jacobi3d",
-                   choices=["jacobi3d", "jacobi3d-to-tol", "bratu-batch", "bratu-warmstart"],
+                   choices=["jacobi3d", "jacobi3d-to-tol", "bratu-batch", "bratu-warmstart", "gemm"],
                    help="jacobi3d: the headline single solve; bratu-batch: 4096 batched Bratu "
                         "solves in one persistent launch; bratu-warmstart: the learned warm "
-                        "start on 256^2 Bratu with source (each reported separately)")
+                        "start on 256^2 Bratu with source; gemm: the warm start's BF16 GEMM on "
+                        "the tcgen05 and mma.sync paths (each reported separately)")
     p.add_argument("--tol-cap", type=int, default=10000)
     p.add_argument("--tol-side", type=int, default=256,
                    help="jacobi3d-to-tol: grid side of the GPU comparison")
@@ -1075,12 +1076,82 @@ def warm_vs_plain_fp64(aa, args, seeds, x0s, s):
     return out
 
 
+def bf16_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured (cuBLAS bf16 burst)"
+    except Exception:
+        return 1900.0, "fallback"
+
+
+def run_gemm(args, ws_, rank, local):
+    """The warm start's GEMM C = A B^T (BF16 in, FP32 accumulate) on the
+    tcgen05 path and the mma.sync path: a large square product and the
+    shapes one training step of the 256^2 network runs (batch 128,
+    65 -> 1024 -> 1024 -> 65536).  CUDA events around `steps` launches after
+    `warmup`; operands are random BF16."""
+    import torch
+    from paper_2110_09667_gb300 import warmstart
+    if rank != 0:
+        return None
+    torch.cuda.set_device(local)
+    peak, src = bf16_peak()
+    shapes = [("square 8192^3", 8192, 8192, 8192, 0),
+              ("output layer forward 128 x 65536 x 1024", 128, 65536, 1024, 0),
+              ("output layer weight gradient 65536 x 1024 x 128", 65536, 1024, 128, 0),
+              ("hidden layer forward 128 x 1024 x 1024 (bias, GELU, bf16)", 128, 1024, 1024, 15),
+              ("output layer data gradient 128 x 1024 x 65536", 128, 1024, 65536, 4)]
+    out = {"metric": "BF16 GEMM TFLOP/s (C = A B^T, FP32 accumulation)", "unit": "TFLOP/s",
+           "peak": peak, "peak_source": src, "steps": args.steps, "warmup": args.warmup,
+           "data": "synthetic (torch.randn BF16)", "shapes": []}
+    g = torch.Generator(device="cuda").manual_seed(0)
+    for name, M, N, K, epi in shapes:
+        A = torch.randn(M, K, device="cuda", generator=g).to(torch.bfloat16)
+        B = torch.randn(N, K, device="cuda", generator=g).to(torch.bfloat16)
+        C = torch.empty(M, N, device="cuda",
+                        dtype=torch.bfloat16 if epi & warmstart.EPI_BF16 else torch.float32)
+        bias = torch.zeros(N, device="cuda") if epi & warmstart.EPI_BIAS else None
+        pre = torch.empty(M, N, device="cuda") if epi & warmstart.EPI_PRE else None
+        row = {"shape": name, "M": M, "N": N, "K": K}
+        ref = None
+        for impl in ("tc", "mma"):
+            def launch():
+                warmstart.gemm_nt(A, B, C, bias=bias, pre=pre, epi=epi, impl=impl)
+            for _ in range(args.warmup):
+                launch()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(args.steps):
+                launch()
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.steps
+            tf = 2.0 * M * N * K / (ms * 1e-3) / 1e12
+            row[impl] = {"ms": round(ms, 4), "tflops": round(tf, 1), "frac": round(tf / peak, 4)}
+            if ref is None:
+                ref = C.float().clone()
+            else:
+                row["max_rel_diff_tc_vs_mma"] = float(
+                    ((C.float() - ref).abs().max() / ref.abs().max().clamp_min(1e-30)).item())
+        warmstart.gemm_tc_status()
+        out["shapes"].append(row)
+    sq = out["shapes"][0]
+    out["value"] = sq["tc"]["tflops"]
+    out["roofline"] = {"bound": "tensor", "achieved": sq["tc"]["tflops"], "peak": peak,
+                       "unit": "TFLOP/s", "frac": sq["tc"]["frac"], "kernel": "gemm_tc_kernel",
+                       "traffic": None}
+    out["higher_is_better"] = True
+    return out
+
+
 def main():
     args = parse()
     ws, rank, local = dist_setup()
-    if args.workload in ("bratu-batch", "bratu-warmstart", "jacobi3d-to-tol"):
+    if args.workload in ("bratu-batch", "bratu-warmstart", "jacobi3d-to-tol", "gemm"):
         run = {"bratu-batch": run_batch, "bratu-warmstart": run_warmstart,
-               "jacobi3d-to-tol": run_to_tol}[args.workload]
+               "jacobi3d-to-tol": run_to_tol, "gemm": run_gemm}[args.workload]
         line = run(args, ws, rank, local)
         if line is not None:
             print(json.dumps(line), flush=True)

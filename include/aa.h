@@ -315,6 +315,21 @@ int aa_exp_fp32pipe(int64_t n, const double *u_dev, double *out_dev, void *strea
  * FP32 C already in place (not with 4). */
 int aa_gemm_bf16_nt(int M, int N, int K, const void *A, int lda, const void *B, int ldb, void *C,
                     int ldc, const float *bias, float *pre, int ldp, int epi, void *stream);
+/* The same product on the fifth-generation tensor cores: tcgen05.mma with
+ * the FP32 accumulator in tensor memory, operands brought into shared memory
+ * by the tensor-memory accelerator (128-byte swizzle), one 128 x 256 (or
+ * 128 x 128) tile of C per CTA.  Same arguments, layout rules and epi bits as
+ * aa_gemm_bf16_nt, and ldc >= N (ldp >= N with epi bit 8).  Rows of C are
+ * the same sums in another order: results agree with aa_gemm_bf16_nt to the
+ * FP32 accumulation bound.  Every device-side wait is bounded (one second);
+ * a CTA that gives up writes NaN over its tile and is reported by
+ * aa_gemm_tc_status. */
+int aa_gemm_bf16_nt_tc(int M, int N, int K, const void *A, int lda, const void *B, int ldb, void *C,
+                       int ldc, const float *bias, float *pre, int ldp, int epi, void *stream);
+/* Synchronises `stream`; AA_ETIMEOUT (and the record cleared) if a CTA of an
+ * aa_gemm_bf16_nt_tc launch gave up a bounded wait since the last call,
+ * else AA_OK. */
+int aa_gemm_tc_status(void *stream);
 /* out[c][r] = in[r][c] for a [rows x cols] BF16 matrix. */
 int aa_transpose_bf16(int rows, int cols, const void *in, int ldi, void *out, int ldo,
                       void *stream);

@@ -28,6 +28,9 @@ def _L():
     if not getattr(L, "_mlp_ready", False):
         vp, i32, i64, f32 = C.c_void_p, C.c_int, C.c_int64, C.c_float
         L.aa_gemm_bf16_nt.argtypes = [i32, i32, i32, vp, i32, vp, i32, vp, i32, vp, vp, i32, i32, vp]
+        L.aa_gemm_bf16_nt_tc.argtypes = [i32, i32, i32, vp, i32, vp, i32, vp, i32, vp, vp, i32, i32,
+                                         vp]
+        L.aa_gemm_tc_status.argtypes = [vp]
         L.aa_transpose_bf16.argtypes = [i32, i32, vp, i32, vp, i32, vp]
         L.aa_gelu_bwd.argtypes = [i64, vp, vp, vp]
         L.aa_mse.argtypes = [i64, vp, vp, f32, vp, vp, i32, vp]
@@ -47,15 +50,57 @@ def _p(t):
 EPI_BIAS, EPI_GELU, EPI_BF16, EPI_PRE, EPI_ACC = 1, 2, 4, 8, 16
 
 
-def gemm_nt(A, B, C_out, *, bias=None, pre=None, epi=0):
+# GEMM implementation used by gemm_nt: "tc" (tcgen05 tensor cores, accumulator
+# in tensor memory) or "mma" (the warp-level mma.sync kernel, kept for comparison)
+GEMM_IMPL = "tc"
+
+
+def _check_gemm(A, B, C_out, bias, pre, epi):
+    """Shapes, strides, dtypes and devices of a gemm_nt call (the C ABI sees
+    only pointers: a short or mistyped buffer would be read or written past
+    its end)."""
+    import torch
+    for t, name in ((A, "A"), (B, "B")):
+        if t.dim() != 2 or t.stride(1) != 1:
+            raise ValueError(f"{name}: expected a 2-D tensor with contiguous rows")
+    if B.shape[1] != A.shape[1]:
+        raise ValueError(f"B: expected {A.shape[1]} columns (K), got {B.shape[1]}")
+    M, N = A.shape[0], B.shape[0]
+    if C_out.dim() != 2 or tuple(C_out.shape) != (M, N) or C_out.stride(1) != 1:
+        raise ValueError(f"C: expected a [{M}, {N}] tensor with contiguous rows")
+    if bias is not None and (bias.dim() != 1 or bias.numel() < N or bias.stride(0) != 1):
+        raise ValueError(f"bias: expected at least {N} contiguous values")
+    if pre is not None and (pre.dim() != 2 or tuple(pre.shape) != (M, N) or pre.stride(1) != 1):
+        raise ValueError(f"pre: expected a [{M}, {N}] tensor with contiguous rows")
+    want_c = torch.bfloat16 if epi & EPI_BF16 else torch.float32
+    for t, name, dt in ((A, "A", torch.bfloat16), (B, "B", torch.bfloat16), (C_out, "C", want_c),
+                        (bias, "bias", torch.float32), (pre, "pre", torch.float32)):
+        if t is not None and t.dtype != dt:
+            raise ValueError(f"{name}: expected {dt}, got {t.dtype}")
+    for t, name in ((A, "A"), (B, "B"), (C_out, "C"), (bias, "bias"), (pre, "pre")):
+        if t is not None and not t.is_cuda:
+            raise ValueError(f"{name}: expected a CUDA tensor, got device {t.device}")
+
+
+def gemm_nt(A, B, C_out, *, bias=None, pre=None, epi=0, impl=None):
     """C = A B^T (A: [M, K] bf16, B: [N, K] bf16)."""
+    _check_gemm(A, B, C_out, bias, pre, epi)
     M, K = A.shape
     N = B.shape[0]
-    rc = _L().aa_gemm_bf16_nt(M, N, K, _p(A), A.stride(0), _p(B), B.stride(0), _p(C_out),
-                              C_out.stride(0), _p(bias), _p(pre),
-                              pre.stride(0) if pre is not None else 0, epi, _stream())
+    impl = impl or GEMM_IMPL
+    L = _L()
+    fn = L.aa_gemm_bf16_nt_tc if impl == "tc" else L.aa_gemm_bf16_nt
+    rc = fn(M, N, K, _p(A), A.stride(0), _p(B), B.stride(0), _p(C_out), C_out.stride(0), _p(bias),
+            _p(pre), pre.stride(0) if pre is not None else 0, epi, _stream())
     if rc != 0:
-        raise AAError(rc, "aa_gemm_bf16_nt")
+        raise AAError(rc, "aa_gemm_bf16_nt_tc" if impl == "tc" else "aa_gemm_bf16_nt")
+
+
+def gemm_tc_status():
+    """Raise AAError(AA_ETIMEOUT) if a tcgen05 GEMM gave up a bounded wait."""
+    rc = _L().aa_gemm_tc_status(_stream())
+    if rc != 0:
+        raise AAError(rc, "aa_gemm_tc_status")
 
 
 def transpose(X, out):

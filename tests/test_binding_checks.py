@@ -58,3 +58,24 @@ def test_vector_checks(aa):
         aa._vec(torch.zeros(8, dtype=torch.float32), 8, "x")
     with pytest.raises(ValueError, match="CUDA"):
         aa._vec(f64(8), 8, "x")
+
+
+def test_gemm_checks(aa):
+    from paper_2110_09667_gb300 import warmstart as ws
+    bf = torch.bfloat16
+    A, B = torch.zeros(4, 16, dtype=bf), torch.zeros(6, 16, dtype=bf)
+    C = torch.zeros(4, 6)
+    with pytest.raises(ValueError, match="columns"):
+        ws.gemm_nt(A, torch.zeros(6, 8, dtype=bf), C)          # K mismatch
+    with pytest.raises(ValueError, match="contiguous rows"):
+        ws.gemm_nt(torch.zeros(16, 4, dtype=bf).t(), B, C)     # strided rows
+    with pytest.raises(ValueError, match=r"\[4, 6\]"):
+        ws.gemm_nt(A, B, torch.zeros(4, 5))                     # C too small
+    with pytest.raises(ValueError, match="bias"):
+        ws.gemm_nt(A, B, C, bias=torch.zeros(5), epi=ws.EPI_BIAS)
+    with pytest.raises(ValueError, match="bfloat16"):
+        ws.gemm_nt(A.float(), B, C)
+    with pytest.raises(ValueError, match="C: expected torch.bfloat16"):
+        ws.gemm_nt(A, B, C, epi=ws.EPI_BF16)                    # BF16 store into an FP32 C
+    with pytest.raises(ValueError, match="CUDA"):
+        ws.gemm_nt(A, B, C, impl="tc")                          # host tensors

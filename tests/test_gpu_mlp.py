@@ -30,18 +30,54 @@ def bf16(a):
     return torch.from_numpy(omlp.round_bf16(a).astype(np.float32)).cuda().to(torch.bfloat16)
 
 
+IMPLS = ["tc", "mma"]
+
+
+def _tc_ok(ws, impl):
+    if impl == "tc":
+        ws.gemm_tc_status()  # raises on a timed-out tcgen05 CTA
+
+
+@pytest.mark.parametrize("impl", IMPLS)
 @pytest.mark.parametrize("M,N,K", [(200, 300, 136), (1, 8, 8), (129, 1, 64), (256, 1024, 72)])
-def test_gemm_nt(ws, M, N, K):
+def test_gemm_nt(ws, impl, M, N, K):
     A = omlp.round_bf16(aa_synth.normal(1, M * K).reshape(M, K))
     B = omlp.round_bf16(aa_synth.normal(2, N * K).reshape(N, K))
     C = torch.empty(M, N, dtype=torch.float32, device="cuda")
-    ws.gemm_nt(bf16(A), bf16(B), C)
+    ws.gemm_nt(bf16(A), bf16(B), C, impl=impl)
+    _tc_ok(ws, impl)
     ref = A @ B.T
     bound = 2 * K * 2.0 ** -24 * (np.abs(A) @ np.abs(B).T)
     assert np.all(np.abs(C.cpu().numpy() - ref) <= bound + 1e-30)
 
 
-def test_gemm_epilogue(ws):
+# tcgen05 path: both tile widths (128 x 256 once the grid has >= 148 such
+# tiles), many K blocks through the stage ring, ragged M, N and K, a leading
+# dimension larger than the row
+@pytest.mark.parametrize("M,N,K,lda", [(1280, 4096, 136, 136), (300, 520, 1000, 1000),
+                                       (130, 257, 8, 16), (128, 1024, 1024, 1032),
+                                       (1300, 4000, 72, 72)])
+def test_gemm_tc_shapes(ws, M, N, K, lda):
+    A = omlp.round_bf16(aa_synth.normal(41, M * K).reshape(M, K))
+    B = omlp.round_bf16(aa_synth.normal(42, N * K).reshape(N, K))
+    Ad = torch.zeros(M, lda, dtype=torch.bfloat16, device="cuda")
+    Ad[:, :K] = bf16(A)
+    C = torch.full((M, N), float("nan"), dtype=torch.float32, device="cuda")
+    ws.gemm_nt(Ad[:, :K], bf16(B), C, impl="tc")
+    ws.gemm_tc_status()
+    ref = A @ B.T
+    bound = 2 * K * 2.0 ** -24 * (np.abs(A) @ np.abs(B).T)
+    c = C.cpu().numpy()
+    assert np.all(np.isfinite(c))
+    assert np.all(np.abs(c - ref) <= bound + 1e-30)
+    # the two tensor-core paths compute the same sums up to their order
+    C2 = torch.empty_like(C)
+    ws.gemm_nt(Ad[:, :K], bf16(B), C2, impl="mma")
+    assert np.all(np.abs(C2.cpu().numpy() - c) <= 2 * bound + 1e-30)
+
+
+@pytest.mark.parametrize("impl", IMPLS)
+def test_gemm_epilogue(ws, impl):
     M, N, K = 70, 90, 40
     A = omlp.round_bf16(aa_synth.normal(3, M * K).reshape(M, K))
     B = omlp.round_bf16(aa_synth.normal(4, N * K).reshape(N, K))
@@ -49,7 +85,8 @@ def test_gemm_epilogue(ws):
     H = torch.empty(M, N, dtype=torch.bfloat16, device="cuda")
     P = torch.empty(M, N, dtype=torch.float32, device="cuda")
     ws.gemm_nt(bf16(A), bf16(B), H, bias=torch.from_numpy(bias).cuda(), pre=P,
-               epi=ws.EPI_BIAS | ws.EPI_GELU | ws.EPI_BF16 | ws.EPI_PRE)
+               epi=ws.EPI_BIAS | ws.EPI_GELU | ws.EPI_BF16 | ws.EPI_PRE, impl=impl)
+    _tc_ok(ws, impl)
     pre = A @ B.T + bias.astype(np.float64)
     assert np.max(np.abs(P.cpu().numpy() - pre)) < 1e-4 * np.abs(pre).max()
     h = H.float().cpu().numpy()
@@ -63,9 +100,11 @@ def test_transpose(ws):
     assert torch.equal(out, X.t().contiguous())
 
 
-def test_mlp_gradients_vs_oracle(ws):
+@pytest.mark.parametrize("impl", IMPLS)
+def test_mlp_gradients_vs_oracle(ws, impl, monkeypatch):
     """Forward output and parameter gradients of the GPU MLP (kernels only)
     against the FP64 oracle MLP, on the same BF16 weights and inputs."""
+    monkeypatch.setattr(ws, "GEMM_IMPL", impl)
     out_dim, hidden, Bn = 48, 64, 32
     net = ws.MLP(out_dim, hidden=hidden, seed=3)
     # the output layer starts at zero in training; give it random weights so
@@ -124,7 +163,8 @@ def test_adam_step(ws):
     assert np.array_equal(Wb.float().cpu().numpy(), omlp.round_bf16(W.cpu().numpy()).astype(np.float32))
 
 
-def test_gemm_accumulate(ws):
+@pytest.mark.parametrize("impl", IMPLS)
+def test_gemm_accumulate(ws, impl):
     """EPI_ACC: C += A B^T onto an FP32 C already in place (the output layer's
     second, low-order weight product)."""
     M, N, K = 50, 70, 48
@@ -132,7 +172,8 @@ def test_gemm_accumulate(ws):
     B = omlp.round_bf16(aa_synth.normal(22, N * K).reshape(N, K))
     C0 = aa_synth.normal(23, M * N).reshape(M, N).astype(np.float32)
     C = torch.from_numpy(C0.copy()).cuda()
-    ws.gemm_nt(bf16(A), bf16(B), C, epi=ws.EPI_ACC)
+    ws.gemm_nt(bf16(A), bf16(B), C, epi=ws.EPI_ACC, impl=impl)
+    _tc_ok(ws, impl)
     ref = C0.astype(np.float64) + A @ B.T
     bound = 2 * (K + 1) * 2.0 ** -24 * (np.abs(A) @ np.abs(B).T + np.abs(C0))
     assert np.all(np.abs(C.cpu().numpy() - ref) <= bound)
