@@ -161,10 +161,21 @@ __device__ __forceinline__ F2 df_axpy_ff(float u, F2 c, F2 a) {
 // ones per row.
 __device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
 
+// a - b per component: the paired subtraction (PTX sub.rn.f32x2), so that
+// no operand has to be negated first.
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  float2 r;
+  asm("{\n .reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
+      " sub.rn.f32x2 rd, ra, rb;\n mov.b64 {%0, %1}, rd;\n}"
+      : "=f"(r.x), "=f"(r.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return r;
+}
+
 __device__ __forceinline__ void two_sum2(float2 a, float2 b, float2 &s, float2 &t) {
   s = __fadd2_rn(a, b);
-  const float2 bb = __fadd2_rn(s, neg2(a));
-  t = __fadd2_rn(__fadd2_rn(a, neg2(__fadd2_rn(s, neg2(bb)))), __fadd2_rn(b, neg2(bb)));
+  const float2 bb = sub2(s, a);
+  t = __fadd2_rn(sub2(a, sub2(s, bb)), sub2(b, bb));
 }
 
 // (S, C) += p + e per component (acc_add on two rows).

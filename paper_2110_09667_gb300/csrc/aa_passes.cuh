@@ -440,10 +440,11 @@ __device__ __forceinline__ void row_program_lp(const PassArgs &a, Stage st, int 
         char *gq = (char *)a.out_q0 + row * (int64_t)sizeof(QT);  // slot j: gq + j * qstride
         const float4 *kq = (const float4 *)(cf + CF_ROT);    // k1 (hi, lo), k2 (hi, lo)
         float w = q2f<QT>(sq[0]);
-        for (int j = 0; j < a.m - 1; ++j) {
+        uint64_t tm = tymask;
+        for (int j = 0; j < a.m - 1; ++j, tm >>= 1) {
           const float u = q2f<QT>(sq[TR]);
           const float4 k = kq[j];
-          const bool ty = (tymask >> j) & 1ull;
+          const bool ty = tm & 1ull;
           const float pa = ty ? u : w, pb = ty ? w : u;
           const QT qs = f2q<QT>(__fmaf_rn(k.x, pa, pb));
           w = __fmaf_rn(k.z, pb, pa);
@@ -1074,6 +1075,104 @@ __device__ __forceinline__ double pow2d(int e) {
   return __hiloint2double((1023 + e) << 20, 0);
 }
 
+// One dot product of the FP32-pipe dot phase (MODES 1-3) over one tile:
+// (S2, C2) += sum over the tile's rows of column ca times column cb, the
+// columns read from the stage as stored history (FP32/BF16, MODE 2) or as
+// (hi, lo) splits of FP64 columns.
+template <class QT, int MODE>
+__device__ __forceinline__ void dot_tile(Stage st, int ca, int cb, int qbase, int rows, int lane,
+                                         float2 &S2, float2 &C2) {
+  const bool qa = (MODE == 2) && ca >= qbase, qb = (MODE == 2) && cb >= qbase;
+  if (rows == TR) {
+    // full tile: lane l takes row pairs 2l + 64h (8-byte history
+    // loads, 16-byte split-pair loads, contiguous across the warp)
+    // and works on both rows with paired FP32 instructions
+    float2 p, e;
+    // MODE 2: the row pairs at even and odd h go to two compensated chains
+    // (the second one merged at the end) so that two independent dependency
+    // chains run per dot
+    float2 Sb = make_float2(0.f, 0.f), Cb = make_float2(0.f, 0.f);
+    if (qa && qb) {
+#pragma unroll
+      for (int h = 0; h < TR / 64; h += 2) {
+        const int r = 2 * lane + 64 * h;
+        const float2 x = q2rows<QT>(st, ca, r), y = q2rows<QT>(st, cb, r);
+        const float2 x1 = q2rows<QT>(st, ca, r + 64), y1 = q2rows<QT>(st, cb, r + 64);
+        p = __fmul2_rn(x, y);
+        const float2 p1 = __fmul2_rn(x1, y1);
+        e = __ffma2_rn(x, y, neg2(p));
+        const float2 e1 = __ffma2_rn(x1, y1, neg2(p1));
+        acc_add2(S2, C2, p, e);
+        acc_add2(Sb, Cb, p1, e1);
+      }
+      acc_add2(S2, C2, Sb, Cb);
+    } else if (qa || qb) {
+      const int cq = qa ? ca : cb, cv = qa ? cb : ca;
+#pragma unroll
+      for (int h = 0; h < TR / 64; h += 2) {
+        const int r = 2 * lane + 64 * h;
+        const float2 q = q2rows<QT>(st, cq, r), q1 = q2rows<QT>(st, cq, r + 64);
+        const float4 v = st.pairs2(cv, r), v1 = st.pairs2(cv, r + 64);
+        float2 p1, e1;
+        prod_f2(make_float2(v.x, v.y), make_float2(v.z, v.w), q, p, e);
+        prod_f2(make_float2(v1.x, v1.y), make_float2(v1.z, v1.w), q1, p1, e1);
+        acc_add2(S2, C2, p, e);
+        acc_add2(Sb, Cb, p1, e1);
+      }
+      acc_add2(S2, C2, Sb, Cb);
+    } else if constexpr (MODE == 1) {
+      // FP64 storage: one compensated pair per dot (registers for
+      // four CTAs per SM, which the FP64 rotation chains need more
+      // than the paired instructions)
+      float S = S2.x, C = C2.x, ps, es;
+#pragma unroll
+      for (int h = 0; h < TR / 64; ++h) {
+        const int r = 2 * lane + 64 * h;
+        const float4 x = st.pairs2(ca, r), y = st.pairs2(cb, r);
+        prod_ff(F2{x.x, x.z}, F2{y.x, y.z}, ps, es);
+        acc_add(S, C, ps, es);
+        prod_ff(F2{x.y, x.w}, F2{y.y, y.w}, ps, es);
+        acc_add(S, C, ps, es);
+      }
+      S2.x = S;
+      C2.x = C;
+    } else {
+#pragma unroll
+      for (int h = 0; h < TR / 64; ++h) {
+        const int r = 2 * lane + 64 * h;
+        const float4 x = st.pairs2(ca, r), y = st.pairs2(cb, r);
+        prod_ff2(make_float2(x.x, x.y), make_float2(x.z, x.w), make_float2(y.x, y.y),
+                 make_float2(y.z, y.w), p, e);
+        acc_add2(S2, C2, p, e);
+      }
+    }
+  } else {
+    // ragged last tile: one row at a time, into the even-row sums
+    float S = S2.x, C = C2.x, p, e;
+    if (qa && qb) {
+      for (int r = lane; r < rows; r += 32) {
+        const float x = q2f<QT>(st.q<QT>(ca)[r]), y = q2f<QT>(st.q<QT>(cb)[r]);
+        p = __fmul_rn(x, y);
+        e = __fmaf_rn(x, y, -p);
+        acc_add(S, C, p, e);
+      }
+    } else if (qa || qb) {
+      const int cq = qa ? ca : cb, cv = qa ? cb : ca;
+      for (int r = lane; r < rows; r += 32) {
+        prod_f(st.f2(cv, r), q2f<QT>(st.q<QT>(cq)[r]), p, e);
+        acc_add(S, C, p, e);
+      }
+    } else {
+      for (int r = lane; r < rows; r += 32) {
+        prod_ff(st.f2(ca, r), st.f2(cb, r), p, e);
+        acc_add(S, C, p, e);
+      }
+    }
+    S2.x = S;
+    C2.x = C;
+  }
+}
+
 // ---------------------------------------------------------------- kernel
 //
 // MODE 0: FP64 storage, FP64 arithmetic throughout (exact FP64 path).
@@ -1250,6 +1349,22 @@ __global__ void __launch_bounds__(NT, (MODE != 0)
     for (int i = 0; i < DPW; ++i) accS[i] = accC[i] = make_float2(0.f, 0.f);
   }
   constexpr int FLUSH = (MODE == 3) ? 4 : 8;  // tiles per fold into FP64
+  // slot i of this warp's dot-phase accumulators holds dot slot_dot(i)
+  auto slot_dot = [&](int i) { return dbase + warp + NWARP * i; };
+  // FP32-pipe forms: fold each lane's float pairs into its FP64 sums (exact
+  // conversions)
+  auto fold_slots = [&](bool reset) {
+    if constexpr (MODE != 0) {
+#pragma unroll
+      for (int i = 0; i < DPW; ++i) {
+        if (slot_dot(i) < a.ndots) {
+          acc[i] += fold_f<MODE>(accS[i].x) + fold_f<MODE>(accS[i].y);
+          acc[i] += fold_f<MODE>(accC[i].x) + fold_f<MODE>(accC[i].y);
+          if (reset) accS[i] = accC[i] = make_float2(0.f, 0.f);
+        }
+      }
+    }
+  };
 
   constexpr bool EARLY_REFILL = (MODE == 1 || MODE == 2);
   int it = 0;
@@ -1339,99 +1454,12 @@ __global__ void __launch_bounds__(NT, (MODE != 0)
             sum = fma(ldv<QT>(st, ca, r, qa), ldv<QT>(st, cb, r, qb), sum);
           acc[i] = sum;
         } else {
-          const bool qa = (MODE == 2) && ca >= a.qbase, qb = (MODE == 2) && cb >= a.qbase;
-          float2 S2 = accS[i], C2 = accC[i];
-          if (rows == TR) {
-            // full tile: lane l takes row pairs 2l + 64h (8-byte history
-            // loads, 16-byte split-pair loads, contiguous across the warp)
-            // and works on both rows with paired FP32 instructions
-            float2 p, e;
-            if (qa && qb) {
-#pragma unroll
-              for (int h = 0; h < TR / 64; ++h) {
-                const int r = 2 * lane + 64 * h;
-                const float2 x = q2rows<QT>(st, ca, r), y = q2rows<QT>(st, cb, r);
-                p = __fmul2_rn(x, y);
-                e = __ffma2_rn(x, y, neg2(p));
-                acc_add2(S2, C2, p, e);
-              }
-            } else if (qa || qb) {
-              const int cq = qa ? ca : cb, cv = qa ? cb : ca;
-#pragma unroll
-              for (int h = 0; h < TR / 64; ++h) {
-                const int r = 2 * lane + 64 * h;
-                const float2 q = q2rows<QT>(st, cq, r);
-                const float4 v = st.pairs2(cv, r);
-                prod_f2(make_float2(v.x, v.y), make_float2(v.z, v.w), q, p, e);
-                acc_add2(S2, C2, p, e);
-              }
-            } else if constexpr (MODE == 1) {
-              // FP64 storage: one compensated pair per dot (registers for
-              // four CTAs per SM, which the FP64 rotation chains need more
-              // than the paired instructions)
-              float S = S2.x, C = C2.x, ps, es;
-#pragma unroll
-              for (int h = 0; h < TR / 64; ++h) {
-                const int r = 2 * lane + 64 * h;
-                const float4 x = st.pairs2(ca, r), y = st.pairs2(cb, r);
-                prod_ff(F2{x.x, x.z}, F2{y.x, y.z}, ps, es);
-                acc_add(S, C, ps, es);
-                prod_ff(F2{x.y, x.w}, F2{y.y, y.w}, ps, es);
-                acc_add(S, C, ps, es);
-              }
-              S2.x = S;
-              C2.x = C;
-            } else {
-#pragma unroll
-              for (int h = 0; h < TR / 64; ++h) {
-                const int r = 2 * lane + 64 * h;
-                const float4 x = st.pairs2(ca, r), y = st.pairs2(cb, r);
-                prod_ff2(make_float2(x.x, x.y), make_float2(x.z, x.w), make_float2(y.x, y.y),
-                         make_float2(y.z, y.w), p, e);
-                acc_add2(S2, C2, p, e);
-              }
-            }
-          } else {
-            // ragged last tile: one row at a time, into the even-row sums
-            float S = S2.x, C = C2.x, p, e;
-            if (qa && qb) {
-              for (int r = lane; r < rows; r += 32) {
-                const float x = q2f<QT>(st.q<QT>(ca)[r]), y = q2f<QT>(st.q<QT>(cb)[r]);
-                p = __fmul_rn(x, y);
-                e = __fmaf_rn(x, y, -p);
-                acc_add(S, C, p, e);
-              }
-            } else if (qa || qb) {
-              const int cq = qa ? ca : cb, cv = qa ? cb : ca;
-              for (int r = lane; r < rows; r += 32) {
-                prod_f(st.f2(cv, r), q2f<QT>(st.q<QT>(cq)[r]), p, e);
-                acc_add(S, C, p, e);
-              }
-            } else {
-              for (int r = lane; r < rows; r += 32) {
-                prod_ff(st.f2(ca, r), st.f2(cb, r), p, e);
-                acc_add(S, C, p, e);
-              }
-            }
-            S2.x = S;
-            C2.x = C;
-          }
-          accS[i] = S2;
-          accC[i] = C2;
+          dot_tile<QT, MODE>(st, ca, cb, a.qbase, rows, lane, accS[i], accC[i]);
         }
       }
     }
     if constexpr (MODE != 0) {
-      if ((it + 1) % FLUSH == 0) {
-#pragma unroll
-        for (int i = 0; i < DPW; ++i) {
-          if (dbase + warp + NWARP * i < a.ndots) {
-            acc[i] += fold_f<MODE>(accS[i].x) + fold_f<MODE>(accS[i].y);
-            acc[i] += fold_f<MODE>(accC[i].x) + fold_f<MODE>(accC[i].y);
-            accS[i] = accC[i] = make_float2(0.f, 0.f);
-          }
-        }
-      }
+      if ((it + 1) % FLUSH == 0) fold_slots(true);
     }
     if (!EARLY_REFILL || nstages == 1) {
       __syncthreads();
@@ -1444,15 +1472,7 @@ __global__ void __launch_bounds__(NT, (MODE != 0)
       }
     }
   }
-  if constexpr (MODE != 0) {
-#pragma unroll
-    for (int i = 0; i < DPW; ++i) {
-      if (dbase + warp + NWARP * i < a.ndots) {
-        acc[i] += fold_f<MODE>(accS[i].x) + fold_f<MODE>(accS[i].y);
-        acc[i] += fold_f<MODE>(accC[i].x) + fold_f<MODE>(accC[i].y);
-      }
-    }
-  }
+  if constexpr (MODE != 0) fold_slots(false);
 
   const bool has_epilogue = a.ndots > 0 || a.kind == K_A || a.kind == K_PROJ;
   if (s_err) {
@@ -1494,7 +1514,7 @@ __global__ void __launch_bounds__(NT, (MODE != 0)
   if (!rowdots && !s_err) {
 #pragma unroll
     for (int i = 0; i < DPW; ++i) {
-      const int d = dbase + warp + NWARP * i;
+      const int d = slot_dot(i);
       double v = acc[i];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
