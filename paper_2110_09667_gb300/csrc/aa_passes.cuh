@@ -441,6 +441,7 @@ __device__ __forceinline__ void row_program_lp(const PassArgs &a, Stage st, int 
         const float4 *kq = (const float4 *)(cf + CF_ROT);    // k1 (hi, lo), k2 (hi, lo)
         float w = q2f<QT>(sq[0]);
         uint64_t tm = tymask;
+#pragma unroll 4
         for (int j = 0; j < a.m - 1; ++j, tm >>= 1) {
           const float u = q2f<QT>(sq[TR]);
           const float4 k = kq[j];
@@ -1173,6 +1174,87 @@ __device__ __forceinline__ void dot_tile(Stage st, int ca, int cb, int qbase, in
   }
 }
 
+// Dot-product families of the FP32/BF16-history form (MODE 2).  A pass's
+// phase dots are q_j . v for history columns q_j (stage column qbase + j) and
+// at most three shared vectors v: NS split FP64 vectors (f, Delta f, or the
+// projected vector; (hi, lo) pairs in the stage) and, with HQ, one history
+// column (q_{k-1}: ICWY's T row, DCGS-2's correction coefficients).  Warp w
+// takes the columns j = w, w + NWARP, w + 2 NWARP (ncw of them) and every
+// vector, so the vectors are loaded once per row pair for all of the warp's
+// columns, each column once for all vectors, and up to nine independent
+// compensated chains run side by side.  A (column, vector) pair without a
+// dot product is computed and dropped.  Accumulator slot 3c + vi belongs to
+// the warp's column c and vector vi (vi = 0, 1 split, 2 history).
+constexpr int FAM_COLS = 3;                 // columns per warp
+constexpr int FAM_SLOTS = 3 * FAM_COLS;     // accumulator slots per lane
+constexpr int FAM_MAXJ = NWARP * FAM_COLS;  // history columns a family may span
+
+template <class QT, int NS, bool HQ>
+__device__ __forceinline__ void fam_tile(Stage st, const int (&col)[FAM_COLS], int ncw, int v0,
+                                         int v1, int vq, int rows, int lane,
+                                         float2 (&S)[FAM_SLOTS], float2 (&C)[FAM_SLOTS]) {
+  if (rows == TR) {
+#pragma unroll
+    for (int h = 0; h < TR / 64; ++h) {
+      const int r = 2 * lane + 64 * h;
+      float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
+      float2 aq = make_float2(0.f, 0.f);
+      if (NS >= 1) a0 = st.pairs2(v0, r);
+      if (NS >= 2) a1 = st.pairs2(v1, r);
+      if (HQ) aq = q2rows<QT>(st, vq, r);
+#pragma unroll
+      for (int c = 0; c < FAM_COLS; ++c) {
+        if (c < ncw) {
+          const float2 x = q2rows<QT>(st, col[c], r);
+          float2 p, e;
+          if (NS >= 1) {
+            prod_f2(make_float2(a0.x, a0.y), make_float2(a0.z, a0.w), x, p, e);
+            acc_add2(S[3 * c], C[3 * c], p, e);
+          }
+          if (NS >= 2) {
+            prod_f2(make_float2(a1.x, a1.y), make_float2(a1.z, a1.w), x, p, e);
+            acc_add2(S[3 * c + 1], C[3 * c + 1], p, e);
+          }
+          if (HQ) {
+            p = __fmul2_rn(x, aq);
+            e = __ffma2_rn(x, aq, neg2(p));
+            acc_add2(S[3 * c + 2], C[3 * c + 2], p, e);
+          }
+        }
+      }
+    }
+  } else {
+    // ragged last tile: one row at a time, into the even-row sums
+    for (int r = lane; r < rows; r += 32) {
+      F2 b0{0.f, 0.f}, b1{0.f, 0.f};
+      float bq = 0.f;
+      if (NS >= 1) b0 = st.f2(v0, r);
+      if (NS >= 2) b1 = st.f2(v1, r);
+      if (HQ) bq = q2f<QT>(st.q<QT>(vq)[r]);
+#pragma unroll
+      for (int c = 0; c < FAM_COLS; ++c) {
+        if (c < ncw) {
+          const float x = q2f<QT>(st.q<QT>(col[c])[r]);
+          float p, e;
+          if (NS >= 1) {
+            prod_f(b0, x, p, e);
+            acc_add(S[3 * c].x, C[3 * c].x, p, e);
+          }
+          if (NS >= 2) {
+            prod_f(b1, x, p, e);
+            acc_add(S[3 * c + 1].x, C[3 * c + 1].x, p, e);
+          }
+          if (HQ) {
+            p = __fmul_rn(x, bq);
+            e = __fmaf_rn(x, bq, -p);
+            acc_add(S[3 * c + 2].x, C[3 * c + 2].x, p, e);
+          }
+        }
+      }
+    }
+  }
+}
+
 // ---------------------------------------------------------------- kernel
 //
 // MODE 0: FP64 storage, FP64 arithmetic throughout (exact FP64 path).
@@ -1216,6 +1298,10 @@ __global__ void __launch_bounds__(NT, (MODE != 0)
   __shared__ uint64_t s_split[2];
   __shared__ int s_n64;
   __shared__ uint64_t s_tymask;  // bit j: form of QRDelete rotation j (MODE 2)
+  // MODE 2 dot-product family: s_fam = {on, split vectors, history vector,
+  // vector columns x3}; s_famd[vi][j] = dot of column j with vector vi (-1: none)
+  __shared__ int s_fam[MODE == 2 ? 6 : 1];
+  __shared__ int16_t s_famd[MODE == 2 ? 3 : 1][MODE == 2 ? FAM_MAXJ : 1];
 
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
@@ -1266,6 +1352,46 @@ __global__ void __launch_bounds__(NT, (MODE != 0)
       s_split[0] = sm;
       s_split[1] = 0ull;
       s_n64 = n64;
+      // dot-product family (fam_tile): every phase dot is (history column,
+      // shared vector) with at most two split vectors and one history vector,
+      // no pair twice, and columns j < FAM_MAXJ
+      int fam = (DPW == 4 || DPW == 8) ? 1 : 0;
+      int vcol[3] = {-1, -1, -1};  // split vectors in slots 0, 1; history vector in slot 2
+      int nsp = 0;
+      for (int v = 0; v < 3; ++v)
+        for (int j = 0; j < FAM_MAXJ; ++j) s_famd[v][j] = -1;
+      for (int d = n64; d < a.ndots && fam; ++d) {
+        const int ca = a.dot_a[d], cb = a.dot_b[d];
+        const int j = ca - a.qbase;
+        if (ca < a.qbase || j >= FAM_MAXJ) {
+          fam = 0;
+          break;
+        }
+        int vi = -1;
+        if (cb >= a.qbase) {
+          if (vcol[2] < 0) vcol[2] = cb;
+          vi = (vcol[2] == cb) ? 2 : -1;
+        } else {
+          for (int v = 0; v < nsp; ++v)
+            if (vcol[v] == cb) vi = v;
+          if (vi < 0 && nsp < 2) {
+            vcol[nsp] = cb;
+            vi = nsp++;
+          }
+        }
+        if (vi < 0 || s_famd[vi][j] >= 0) {
+          fam = 0;
+          break;
+        }
+        s_famd[vi][j] = (int16_t)d;
+      }
+      if (n64 >= a.ndots || nsp == 0) fam = 0;
+      s_fam[0] = fam;
+      s_fam[1] = nsp;
+      s_fam[2] = vcol[2] >= 0 ? 1 : 0;
+      s_fam[3] = vcol[0];
+      s_fam[4] = vcol[1];
+      s_fam[5] = vcol[2];
     }
   }
   __syncthreads();
@@ -1329,10 +1455,18 @@ __global__ void __launch_bounds__(NT, (MODE != 0)
     }
   }
 
-  double acc[DPW];
+  // slots of per-lane dot-phase accumulators; the MODE 2 family form
+  // (fam_tile) needs FAM_SLOTS of them
+  constexpr int NSLOT = (MODE == 2 && (DPW == 4 || DPW == 8)) ? FAM_SLOTS : DPW;
+  // FP64 sums of the dot phase: per lane in registers (MODES 0, 1, 3), or,
+  // for MODE 2, summed over the warp at each fold into shared memory (frees
+  // the registers for the family form's nine chains)
+  constexpr bool SACC = (MODE == 2);
+  double acc[SACC ? 1 : DPW];
+  __shared__ double s_acc[SACC ? NWARP : 1][SACC ? NSLOT : 1];
   // FP32-pipe partial sums: (S, C) compensated pairs, one per row parity
   // (.x even rows, .y odd rows) so that full tiles use paired instructions
-  float2 accS[MODE ? DPW : 1], accC[MODE ? DPW : 1];
+  float2 accS[MODE ? NSLOT : 1], accC[MODE ? NSLOT : 1];
   constexpr int NRD = ((DPW == 1 && MODE == 0) || MODE == 1 || MODE == 2) ? RD : 1;
   // every dot product accumulated row by row in FP64 (no dot phase)
   const bool rowdots = ((DPW == 1) && (MODE == 0) && a.ndots <= RD) ||
@@ -1343,23 +1477,55 @@ __global__ void __launch_bounds__(NT, (MODE != 0)
 #pragma unroll
   for (int d = 0; d < NRD; ++d) racc[d] = 0.0;
 #pragma unroll
-  for (int i = 0; i < DPW; ++i) acc[i] = 0.0;
+  for (int i = 0; i < (SACC ? 1 : DPW); ++i) acc[i] = 0.0;
+  if constexpr (SACC) {
+    for (int i = lane; i < NSLOT; i += 32) s_acc[warp][i] = 0.0;
+  }
   if constexpr (MODE != 0) {
 #pragma unroll
-    for (int i = 0; i < DPW; ++i) accS[i] = accC[i] = make_float2(0.f, 0.f);
+    for (int i = 0; i < NSLOT; ++i) accS[i] = accC[i] = make_float2(0.f, 0.f);
   }
   constexpr int FLUSH = (MODE == 3) ? 4 : 8;  // tiles per fold into FP64
+  // MODE 2 family form: this warp's columns (fam_tile)
+  const bool famon = (MODE == 2) && !rowdots && s_fam[0] != 0;
+  int fcol[FAM_COLS];
+  int ncw = 0;
+  if constexpr (MODE == 2) {
+#pragma unroll
+    for (int c = 0; c < FAM_COLS; ++c) {
+      const int j = warp + NWARP * c;
+      fcol[c] = a.qbase + j;
+      if (famon && (s_famd[0][j] >= 0 || s_famd[1][j] >= 0 || s_famd[2][j] >= 0)) ncw = c + 1;
+    }
+  }
   // slot i of this warp's dot-phase accumulators holds dot slot_dot(i)
-  auto slot_dot = [&](int i) { return dbase + warp + NWARP * i; };
-  // FP32-pipe forms: fold each lane's float pairs into its FP64 sums (exact
-  // conversions)
+  // (a.ndots: none)
+  auto slot_dot = [&](int i) -> int {
+    if constexpr (MODE == 2) {
+      if (famon) {
+        const int d = s_famd[i % 3][warp + NWARP * (i / 3)];
+        return d >= 0 ? d : a.ndots;
+      }
+    }
+    return i < DPW ? min(dbase + warp + NWARP * i, (int)a.ndots) : (int)a.ndots;
+  };
+  // FP32-pipe forms: fold the per-lane float pairs into FP64 (exact
+  // conversions); MODE 2 sums them over the warp (fixed butterfly) into
+  // s_acc, the other forms keep per-lane sums
   auto fold_slots = [&](bool reset) {
     if constexpr (MODE != 0) {
 #pragma unroll
-      for (int i = 0; i < DPW; ++i) {
+      for (int i = 0; i < NSLOT; ++i) {
         if (slot_dot(i) < a.ndots) {
-          acc[i] += fold_f<MODE>(accS[i].x) + fold_f<MODE>(accS[i].y);
-          acc[i] += fold_f<MODE>(accC[i].x) + fold_f<MODE>(accC[i].y);
+          if constexpr (SACC) {
+            double v = (fold_f<MODE>(accS[i].x) + fold_f<MODE>(accS[i].y)) +
+                       (fold_f<MODE>(accC[i].x) + fold_f<MODE>(accC[i].y));
+            v = warp_sum(v);
+            if (lane == 0) s_acc[warp][i] += v;
+          } else {
+            acc[i] += fold_f<MODE>(accS[i].x) + fold_f<MODE>(accS[i].y);
+            acc[i] += fold_f<MODE>(accC[i].x) + fold_f<MODE>(accC[i].y);
+          }
           if (reset) accS[i] = accC[i] = make_float2(0.f, 0.f);
         }
       }
@@ -1440,10 +1606,22 @@ __global__ void __launch_bounds__(NT, (MODE != 0)
       }
     }
     if (!rowdots) __syncthreads();
+    if constexpr (MODE == 2 && NSLOT == FAM_SLOTS) {
+      if (famon && ncw > 0) {
+        const int v0 = s_fam[3], v1 = s_fam[4], vq = s_fam[5];
+        if (s_fam[1] == 2) {
+          if (s_fam[2]) fam_tile<QT, 2, true>(st, fcol, ncw, v0, v1, vq, rows, lane, accS, accC);
+          else fam_tile<QT, 2, false>(st, fcol, ncw, v0, v1, vq, rows, lane, accS, accC);
+        } else {
+          if (s_fam[2]) fam_tile<QT, 1, true>(st, fcol, ncw, v0, v1, vq, rows, lane, accS, accC);
+          else fam_tile<QT, 1, false>(st, fcol, ncw, v0, v1, vq, rows, lane, accS, accC);
+        }
+      }
+    }
     // dot phase: warp w owns dots w, w + NWARP, ...
 #pragma unroll
     for (int i = 0; i < DPW; ++i) {
-      if (rowdots) break;
+      if (rowdots || famon) break;
       const int d = dbase + warp + NWARP * i;
       if (d < a.ndots) {
         const int ca = sda[d], cb = sdb[d];
@@ -1513,11 +1691,16 @@ __global__ void __launch_bounds__(NT, (MODE != 0)
   }
   if (!rowdots && !s_err) {
 #pragma unroll
-    for (int i = 0; i < DPW; ++i) {
+    for (int i = 0; i < NSLOT; ++i) {
       const int d = slot_dot(i);
-      double v = acc[i];
+      double v;
+      if constexpr (SACC) {
+        v = s_acc[warp][i];  // lane 0 wrote it and reads it below
+      } else {
+        v = acc[i];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      }
       if (lane == 0 && d < a.ndots) {
         if constexpr (MODE == 1) v *= pow2d(-(s_cexp[a.dot_a[d]] + s_cexp[a.dot_b[d]]));
         a.partials[(size_t)blockIdx.x * NDOT_MAX + d] = v;
