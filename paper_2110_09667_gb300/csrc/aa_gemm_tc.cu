@@ -352,6 +352,183 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   if (threadIdx.x == 0 && !good) atomicExch(&g_tc_timeout, 1);
 }
 
+
+// Persistent form for grids of more tiles than SMs: one CTA per SM walks the
+// tiles tile = blockIdx.x + i gridDim.x.  Warp 0 (one thread) keeps the
+// stage ring full across tile boundaries, warp 1 (one thread) issues the MMAs
+// of tile i into accumulator i % 2 of two in tensor memory (2 BN columns),
+// and warps 2-5 read accumulator i % 2 back while the MMAs of tile i + 1 run
+// into the other one.  Accumulator hand-off: tfull[a] (tcgen05.commit after
+// the tile's last MMA) and tempty[a] (one arrive per epilogue warp after its
+// last tcgen05.ld of the tile).  Epilogue warp w reads TMEM lanes
+// 32 (w % 4) .. 32 (w % 4) + 31.  Waits, abort and clean-up as in
+// gemm_tc_kernel.
+constexpr int TCP_THREADS = 192;
+
+__device__ __forceinline__ void mb_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+template <int BN>
+__global__ void __launch_bounds__(TCP_THREADS, 1)
+    gemm_tcp_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                    int M, int N, int K, void *C, int ldc, const float *__restrict__ bias, float *P,
+                    int ldp, int epi) {
+  using Cfg = TcCfg<BN>;
+  constexpr int S = Cfg::STAGES;
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t bar_full[S], bar_empty[S], bar_tfull[2], bar_tempty[2], bar_done;
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_abort;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t base = (su32(smem_raw) + 1023u) & ~1023u;
+  const int tiles_n = (N + BN - 1) / BN;
+  const int ntiles = tiles_n * ((M + TC_BM - 1) / TC_BM);
+  const int nk = (K + TC_BK - 1) / TC_BK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mb_init(su32(&bar_full[s]), 1);
+      mb_init(su32(&bar_empty[s]), 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mb_init(su32(&bar_tfull[a]), 1);
+      mb_init(su32(&bar_tempty[a]), 4);
+    }
+    mb_init(su32(&bar_done), 1);
+    s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     su32(&s_tmem)),
+                 "r"((uint32_t)(2 * BN))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+  bool good = true;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int g = 0;  // K blocks issued so far, over all tiles
+      for (int tile = blockIdx.x; tile < ntiles && !s_abort; tile += gridDim.x) {
+        const int m0 = (tile / tiles_n) * TC_BM, n0 = (tile % tiles_n) * BN;
+        for (int kb = 0; kb < nk; ++kb, ++g) {
+          const int s = g % S;
+          if (g >= S && !mb_wait(su32(&bar_empty[s]), ((g / S) & 1) ^ 1, &s_abort)) {
+            s_abort = 1;
+            break;
+          }
+          const uint32_t full = su32(&bar_full[s]);
+          const uint32_t dst = base + (uint32_t)s * Cfg::STAGE_BYTES;
+          mb_expect_tx(full, Cfg::STAGE_BYTES);
+          tma_load_2d(dst, &tmA, kb * TC_BK, m0, full);
+          tma_load_2d(dst + Cfg::A_BYTES, &tmB, kb * TC_BK, n0, full);
+        }
+      }
+      if (s_abort) {  // let the copies already issued land before the CTA exits
+        for (int j = (g > S ? g - S : 0); j < g; ++j)
+          (void)mb_wait(su32(&bar_full[j % S]), (j / S) & 1, nullptr);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16<BN>();
+      int g = 0, i = 0;
+      for (int tile = blockIdx.x; tile < ntiles && !s_abort; tile += gridDim.x, ++i) {
+        const int acc = i & 1;
+        // the epilogue has drained this accumulator's previous tile
+        if (i >= 2 && !mb_wait(su32(&bar_tempty[acc]), ((i >> 1) & 1) ^ 1, &s_abort)) {
+          s_abort = 1;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d = tmem + (uint32_t)(acc * BN);
+        bool ok = true;
+        for (int kb = 0; kb < nk; ++kb, ++g) {
+          const int s = g % S;
+          if (!mb_wait(su32(&bar_full[s]), (g / S) & 1, &s_abort)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a0 = base + (uint32_t)s * Cfg::STAGE_BYTES, b0 = a0 + Cfg::A_BYTES;
+#pragma unroll
+          for (int k = 0; k < TC_BK / 16; ++k)
+            umma_bf16(d, sw128_desc(a0 + 32u * k), sw128_desc(b0 + 32u * k), idesc,
+                      (kb | k) != 0 ? 1u : 0u);
+          umma_commit(su32(&bar_empty[s]));
+        }
+        if (!ok) {
+          s_abort = 1;
+          break;
+        }
+        umma_commit(su32(&bar_tfull[acc]));
+      }
+      umma_commit(su32(&bar_done));  // arrives once every MMA issued above has completed
+      (void)mb_wait(su32(&bar_done), 0, nullptr);
+    }
+  } else {
+    const int q = warp & 3;  // TMEM lane quarter of this warp
+    const bool vec32 = ((ldc & 3) == 0) && (((uintptr_t)C & 15u) == 0);
+    const bool vec16 = ((ldc & 7) == 0) && (((uintptr_t)C & 15u) == 0);
+    const bool vecp = P && ((ldp & 3) == 0) && (((uintptr_t)P & 15u) == 0);
+    int i = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
+      const int acc = i & 1;
+      good = __all_sync(0xffffffffu, mb_wait(su32(&bar_tfull[acc]), (i >> 1) & 1, &s_abort));
+      if (!good) {
+        if (lane == 0) s_abort = 1;  // stop the other roles too
+        break;
+      }
+      tc_fence_after();
+      const int m0 = (tile / tiles_n) * TC_BM, n0 = (tile % tiles_n) * BN;
+      const int row = m0 + q * 32 + lane;
+      const uint32_t trow = tmem + (uint32_t)(acc * BN) + ((uint32_t)(q * 32) << 16);
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        if (n0 + c0 >= N) break;  // warp-uniform
+        float v[32];
+        tmem_ld32(trow + (uint32_t)c0, v);
+        if (row < M) store_chunk(v, row, n0 + c0, N, C, ldc, bias, P, ldp, epi, vec32, vec16, vecp);
+        __syncwarp();
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mb_arrive(su32(&bar_tempty[acc]));
+    }
+    if (!good) {
+      // tiles this warp did not finish: NaN over its rows of them
+      for (int tile = blockIdx.x + i * (int)gridDim.x; tile < ntiles; tile += gridDim.x) {
+        const int m0 = (tile / tiles_n) * TC_BM, n0 = (tile % tiles_n) * BN;
+        const int row = m0 + q * 32 + lane;
+        for (int c0 = 0; c0 < BN && n0 + c0 < N; c0 += 32) {
+          float v[32];
+#pragma unroll
+          for (int k = 0; k < 32; ++k) v[k] = __int_as_float(0x7fc00000);
+          if (row < M)
+            store_chunk(v, row, n0 + c0, N, C, ldc, nullptr, P, ldp, epi & ~(1 | 2 | 16), vec32,
+                        vec16, vecp);
+        }
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"((uint32_t)(2 * BN))
+                 : "memory");
+  }
+  if (threadIdx.x == 64 && s_abort) atomicExch(&g_tc_timeout, 1);
+}
+
 // ------------------------------------------------------------------- host
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
@@ -387,6 +564,15 @@ bool make_map(CUtensorMap *map, const void *ptr, int rows, int K, int ld, int bo
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// SMs of the current device (0 if the query fails).
+int sm_count() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return 0;
+  return n;
+}
+
 template <int BN>
 int launch_tc(int M, int N, int K, const void *A, int lda, const void *B, int ldb, void *C, int ldc,
               const float *bias, float *pre, int ldp, int epi, cudaStream_t stream) {
@@ -398,8 +584,18 @@ int launch_tc(int M, int N, int K, const void *A, int lda, const void *B, int ld
   if (!make_map(&ma, A, M, K, lda, TC_BM) || !make_map(&mb, B, N, K, ldb, BN)) return AA_ECUDA;
   dim3 grid((N + BN - 1) / BN, (M + TC_BM - 1) / TC_BM);
   if (grid.y > 65535) return AA_EINVAL;
-  gemm_tc_kernel<BN><<<grid, TC_THREADS, Cfg::SMEM, stream>>>(ma, mb, M, N, K, C, ldc, bias, pre,
-                                                              ldp, epi);
+  const int nsm = sm_count();
+  if (nsm > 0 && (long)grid.x * grid.y > 2L * nsm) {
+    // more than two waves of tiles: the persistent form, one CTA per SM
+    if (cudaFuncSetAttribute(gemm_tcp_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             Cfg::SMEM) != cudaSuccess)
+      return AA_ECUDA;
+    gemm_tcp_kernel<BN><<<nsm, TCP_THREADS, Cfg::SMEM, stream>>>(ma, mb, M, N, K, C, ldc, bias, pre,
+                                                                 ldp, epi);
+  } else {
+    gemm_tc_kernel<BN><<<grid, TC_THREADS, Cfg::SMEM, stream>>>(ma, mb, M, N, K, C, ldc, bias, pre,
+                                                                ldp, epi);
+  }
   return cudaGetLastError() == cudaSuccess ? AA_OK : AA_ECUDA;
 }
 

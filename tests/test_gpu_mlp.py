@@ -53,10 +53,12 @@ def test_gemm_nt(ws, impl, M, N, K):
 
 # tcgen05 path: both tile widths (128 x 256 once the grid has >= 148 such
 # tiles), many K blocks through the stage ring, ragged M, N and K, a leading
-# dimension larger than the row
+# dimension larger than the row, and the persistent form (more than two
+# tiles per SM: 336 tiles of 128 x 256, 313 of 128 x 128)
 @pytest.mark.parametrize("M,N,K,lda", [(1280, 4096, 136, 136), (300, 520, 1000, 1000),
                                        (130, 257, 8, 16), (128, 1024, 1024, 1032),
-                                       (1300, 4000, 72, 72)])
+                                       (1300, 4000, 72, 72), (2577, 4056, 200, 200),
+                                       (40003, 120, 64, 72)])
 def test_gemm_tc_shapes(ws, M, N, K, lda):
     A = omlp.round_bf16(aa_synth.normal(41, M * K).reshape(M, K))
     B = omlp.round_bf16(aa_synth.normal(42, N * K).reshape(N, K))

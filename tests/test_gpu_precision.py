@@ -100,3 +100,29 @@ def test_bf16_storage_probe(aa, ora):
     rc, st, x = converge(aa, n, 10, "cgs2", "bf16", "aa_g_jacobi3d", P, scale, 5000)
     res = np.linalg.norm(ora.g_jacobi3d(nx, ny, nz, 0.1, 0.01, 0.8, b, x) - x) / scale
     assert rc == 0 and res < 1.01e-8
+
+
+@pytest.mark.parametrize("m", [5, 10, 20])
+@pytest.mark.parametrize("orth", VARIANTS)
+def test_fp32_storage_qradd_multitile(aa, ora, orth, m):
+    """QRAdd alone (the first pass in its unit-vector form, plus the
+    projection) with FP32 history, at m = 5, 10 and 20 (both slot buckets of
+    the column-family dot phase) on 300,001 rows (1,172 tiles: several per
+    CTA, a ragged last tile): Q and R after m + 3 adds (three deletes) against
+    the oracle with the same FP32 storage rounding.  Stored entries may differ
+    by an FP32 unit where the two sides round at different points, and the
+    device rotates in FP32 (reading 11), so the bound is 1e-4 of the largest
+    entry."""
+    n = 300_001
+    adds = m + 3
+    V = aa_synth.uniform(70 + m, adds * n).reshape(adds, n)
+    O = ora.Oracle(n, m, orth, store_round=1)
+    G = aa.Anderson(n, m, orth, "fp32")
+    for j in range(adds):
+        assert O.qradd(V[j]) == ora.OK
+        assert G.qradd(dev(V[j])) == 0
+    Qo, Ro, _ = O.get_qr()
+    Qg, Rg, _ = G.get_qr()
+    assert Qg.shape == Qo.shape
+    assert np.max(np.abs(Rg - Ro)) <= 1e-4 * np.abs(Ro).max(), orth
+    assert np.max(np.abs(Qg - Qo)) <= 1e-4 * np.abs(Qo).max(), orth
