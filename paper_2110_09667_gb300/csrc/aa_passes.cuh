@@ -1338,9 +1338,17 @@ __global__ void __launch_bounds__(NT, (MODE != 0)
   }
   if constexpr (MODE == 2) {
     // leading dots of two FP64 vectors: FP64 row-local sums; FP64 columns
-    // that meet a history column in a later dot are split for the dot phase
+    // that meet a history column in a later dot are split for the dot phase.
+    // A pass with at most RD dots whose operands are all history columns or
+    // FP64 columns 0 and 1 (an MGS link, a projection) takes every dot as an
+    // FP64 row-local sum (history entries converted exactly), and so has no
+    // dot phase and no barrier before it.
     if (tid == 0) {
       int n64 = 0;
+      bool rowable = a.ndots <= RD;
+      for (int d = 0; d < a.ndots && rowable; ++d)
+        rowable = (a.dot_a[d] >= a.qbase || a.dot_a[d] < 2) && (a.dot_b[d] >= a.qbase || a.dot_b[d] < 2);
+      if (rowable) n64 = a.ndots;
       while (n64 < a.ndots && n64 < RD && a.dot_a[n64] < a.qbase && a.dot_b[n64] < a.qbase &&
              a.dot_a[n64] < 2 && a.dot_b[n64] < 2)
         ++n64;
@@ -1571,7 +1579,11 @@ __global__ void __launch_bounds__(NT, (MODE != 0)
 #pragma unroll
         for (int d = 0; d < NRD; ++d) {
           if (d < dbase) {
-            const double va = sda[d] ? dv1 : dv0, vb = sdb[d] ? dv1 : dv0;
+            // FP64 columns 0, 1 are the row program's dv0, dv1; history
+            // entries are read from the stage and converted exactly
+            const int ca = sda[d], cb = sdb[d];
+            const double va = ca >= a.qbase ? to_d<QT>(st.q<QT>(ca)[tid]) : (ca ? dv1 : dv0);
+            const double vb = cb >= a.qbase ? to_d<QT>(st.q<QT>(cb)[tid]) : (cb ? dv1 : dv0);
             racc[d] = fma(va, vb, racc[d]);
           }
         }
