@@ -1139,8 +1139,10 @@ def run_gemm(args, ws_, rank, local):
         out["shapes"].append(row)
     sq = out["shapes"][0]
     out["value"] = sq["tc"]["tflops"]
+    # 8192^3 has 2,048 tiles of 128 x 256: more than two per SM, so the
+    # library runs its persistent form
     out["roofline"] = {"bound": "tensor", "achieved": sq["tc"]["tflops"], "peak": peak,
-                       "unit": "TFLOP/s", "frac": sq["tc"]["frac"], "kernel": "gemm_tc_kernel",
+                       "unit": "TFLOP/s", "frac": sq["tc"]["frac"], "kernel": "gemm_tcp_kernel",
                        "traffic": None}
     out["higher_is_better"] = True
     return out

@@ -376,9 +376,11 @@ template <class QT>
 __device__ __forceinline__ double lp_chain(Stage st, const float *c, int qb, int cnt, int r) {
   float s0 = 0.f, s1 = 0.f, sl = 0.f;
   int j = 0;
-  for (; j + 1 < cnt; j += 2) {
+  const QT *qp = st.q<QT>(qb) + r;
+#pragma unroll 2
+  for (; j + 1 < cnt; j += 2, qp += 2 * TR) {
     const float2 c0 = *(const float2 *)(c + 2 * j), c1 = *(const float2 *)(c + 2 * j + 2);
-    const float q0 = q2f<QT>(st.q<QT>(qb + j)[r]), q1 = q2f<QT>(st.q<QT>(qb + j + 1)[r]);
+    const float q0 = q2f<QT>(qp[0]), q1 = q2f<QT>(qp[TR]);
     s0 = __fmaf_rn(c0.x, q0, s0);
     s1 = __fmaf_rn(c1.x, q1, s1);
     sl = __fmaf_rn(c0.y, q0, sl);
@@ -386,7 +388,7 @@ __device__ __forceinline__ double lp_chain(Stage st, const float *c, int qb, int
   }
   if (j < cnt) {
     const float2 cc = *(const float2 *)(c + 2 * j);
-    const float q0 = q2f<QT>(st.q<QT>(qb + j)[r]);
+    const float q0 = q2f<QT>(qp[0]);
     s0 = __fmaf_rn(cc.x, q0, s0);
     sl = __fmaf_rn(cc.y, q0, sl);
   }
@@ -497,14 +499,14 @@ __device__ __forceinline__ void row_program_lp(const PassArgs &a, Stage st, int 
       const double y = st.d(0)[r] + lp_chain<QT>(st, cf + CF_COEF, a.qbase, a.k, r);
       a.out_df[row] = y;
       dv0 = y;
-      st.put(0, r, d2f2(y));
+      if (split & 1u) st.put(0, r, d2f2(y));
       break;
     }
     case K_MGS: {
       const double v = st.d(0)[r] + lp_chain<QT>(st, cf + CF_COEF + 2 * (a.jm - 1), a.qbase, 1, r);
       a.out_df[row] = v;
       dv0 = v;
-      st.put(0, r, d2f2(v));
+      if (split & 1u) st.put(0, r, d2f2(v));
       break;
     }
     case K_UPDATE: {
@@ -514,7 +516,8 @@ __device__ __forceinline__ void row_program_lp(const PassArgs &a, Stage st, int 
       break;
     }
     case K_LSQ: {
-      st.put(0, r, d2f2(st.d(0)[r]));
+      dv0 = st.d(0)[r];
+      if (split & 1u) st.put(0, r, d2f2(dv0));
       break;
     }
     default:

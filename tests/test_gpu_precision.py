@@ -126,3 +126,23 @@ def test_fp32_storage_qradd_multitile(aa, ora, orth, m):
     assert Qg.shape == Qo.shape
     assert np.max(np.abs(Rg - Ro)) <= 1e-4 * np.abs(Ro).max(), orth
     assert np.max(np.abs(Qg - Qo)) <= 1e-4 * np.abs(Qo).max(), orth
+
+
+@pytest.mark.parametrize("m", [3, 8])
+@pytest.mark.parametrize("orth", ["icwy", "mgs"])
+def test_fp32_storage_lsq(aa, ora, orth, m):
+    """The least-squares solve R gamma = Q^T f alone (aa_lsq) with FP32
+    history, after m + 2 adds on 70,001 rows: m = 3 takes its dot products
+    as FP64 row sums (at most four of them), m = 8 through the dot phase.
+    gamma against the oracle with the same FP32 storage rounding."""
+    n = 70_001
+    V = aa_synth.uniform(90 + m, (m + 2) * n).reshape(m + 2, n)
+    f = aa_synth.uniform(91 + m, n)
+    O = ora.Oracle(n, m, orth, store_round=1)
+    G = aa.Anderson(n, m, orth, "fp32")
+    for j in range(m + 2):
+        assert O.qradd(V[j]) == ora.OK
+        assert G.qradd(dev(V[j])) == 0
+    go = O.lsq(f)
+    gg = G.lsq(dev(f))
+    assert np.max(np.abs(gg - go)) <= 1e-4 * np.abs(go).max(), (orth, m)
