@@ -222,6 +222,20 @@ int aa_mdot(const double *A_dev, int64_t lda, int k, const double *V_dev, int64_
 int aa_mdot_noalloc(const double *A_dev, int64_t lda, int k, const double *V_dev, int64_t ldv,
                     int nv, int64_t n, double *out_dev, void *stream);
 
+/* Copies `bytes` bytes from src to dst on `stream` (asynchronous).  No
+ * counterpart in the paper: it moves iterates between page-locked host
+ * memory and the device for callers that keep x on the host.  Either side
+ * may be device memory or host memory from cudaHostAlloc/cudaHostRegister;
+ * when the device can address both (cudaPointerGetAttributes reports a
+ * device address) and both are 16-byte aligned, a kernel on every SM does
+ * the copy with 16-byte loads and stores (over this part's NVLink-C2C host
+ * link, faster than the copy engines); otherwise cudaMemcpyAsync does it.
+ * Errors: AA_EINVAL (NULL pointer), AA_ECUDA. */
+int aa_copy(void *dst, const void *src, size_t bytes, void *stream);
+/* 1 if aa_copy(dst, src, ...) takes the kernel path (the device addresses
+ * both sides, 16-byte aligned), 0 if it hands the copy to cudaMemcpyAsync. */
+int aa_copy_path(const void *dst, const void *src);
+
 /* ---------------------------------------------------------- test problems
  * Built-in fixed-point maps (aa_g_fn-compatible) for the seeded stencil
  * workloads.  `user` points to the matching parameter struct; b/src are

@@ -93,6 +93,8 @@ def lib():
                               C.c_int64, _dp, C.c_void_p]
         L.aa_mdot_noalloc.argtypes = [C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_int64,
                                       C.c_int, C.c_int64, C.c_void_p, C.c_void_p]
+        L.aa_copy.argtypes = [C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]
+        L.aa_copy_path.argtypes = [C.c_void_p, C.c_void_p]
         for nm in ("aa_g_jacobi2d", "aa_g_jacobi3d", "aa_g_bratu2d"):
             getattr(L, nm).argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]
         L.aa_last_error.restype = C.c_char_p
@@ -292,6 +294,25 @@ def mdot_noalloc(A, V, out):
     if rc != AA_OK:
         raise AAError(rc, "aa_mdot_noalloc failed")
     return out
+
+
+def copy(dst, src):
+    """aa_copy: dst <- src (same dtype and element count, contiguous; device
+    or page-locked host tensors) on the current stream, by the library's copy
+    kernel where the device can address both sides."""
+    if dst.dtype != src.dtype:
+        raise ValueError(f"copy: dtypes differ ({dst.dtype}, {src.dtype})")
+    if dst.numel() != src.numel():
+        raise ValueError(f"copy: sizes differ ({dst.numel()}, {src.numel()})")
+    if not (dst.is_contiguous() and src.is_contiguous()):
+        raise ValueError("copy: tensors must be contiguous")
+    for t, name in ((dst, "dst"), (src, "src")):
+        if not (t.is_cuda or t.is_pinned()):
+            raise ValueError(f"copy: {name} must be a CUDA or page-locked host tensor")
+    rc = lib().aa_copy(_ptr(dst), _ptr(src), dst.numel() * dst.element_size(), _stream())
+    if rc != AA_OK:
+        raise AAError(rc, "aa_copy failed")
+    return dst
 
 
 class BatchDesc(C.Structure):
