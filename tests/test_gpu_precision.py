@@ -111,7 +111,7 @@ def test_fp32_storage_qradd_multitile(aa, ora, orth, m):
     CTA, a ragged last tile): Q and R after m + 3 adds (three deletes) against
     the oracle with the same FP32 storage rounding.  Stored entries may differ
     by an FP32 unit where the two sides round at different points, and the
-    device rotates in FP32 (reading 11), so the bound is 1e-4 of the largest
+    device rotates in FP32 (float multipliers), so the bound is 1e-4 of the largest
     entry."""
     n = 300_001
     adds = m + 3
