@@ -79,3 +79,15 @@ def test_gemm_checks(aa):
         ws.gemm_nt(A, B, C, epi=ws.EPI_BF16)                    # BF16 store into an FP32 C
     with pytest.raises(ValueError, match="CUDA"):
         ws.gemm_nt(A, B, C, impl="tc")                          # host tensors
+
+
+def test_copy_checks(aa):
+    a = torch.zeros(10, dtype=torch.float64)
+    with pytest.raises(ValueError, match="sizes differ"):
+        aa.copy(a, torch.zeros(9, dtype=torch.float64))
+    with pytest.raises(ValueError, match="dtypes differ"):
+        aa.copy(a, torch.zeros(10, dtype=torch.float32))
+    with pytest.raises(ValueError, match="contiguous"):
+        aa.copy(torch.zeros(20, dtype=torch.float64)[::2], a)
+    with pytest.raises(ValueError, match="page-locked"):
+        aa.copy(a, torch.zeros(10, dtype=torch.float64))        # pageable host tensors
